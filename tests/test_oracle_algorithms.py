@@ -1,0 +1,242 @@
+"""Pins for the oracle's algorithms: GS, multi-plane GS, OSPR (with Philox) and gradient descent.
+
+* GS: Fienup's error-reduction property (the replay-amplitude error never increases, for every
+  projection and for Fourier and Fresnel), the fixed point of an exactly reachable target, and one
+  8x8 iteration by the explicit quadruple DFT sum.
+* Multi-plane GS: P = 1 reduces to GS; the product-space error never increases.
+* OSPR: Philox known-answer vectors, Hermitian replay of a real hologram, bit packing, the NMSE trend
+  over subframes.
+* GD: central finite differences of the loss, an independent float64 autograd of the same loss
+  (library, test only), Adam against torch.optim.Adam.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import dft, gd, gs, optics, ospr, philox, project
+import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+LAM, PITCH = 532e-9, 8e-6
+
+
+# ------------------------------------------------------------------ GS
+
+
+@pytest.mark.parametrize("n_levels", [0, 2, 4, 8])
+@pytest.mark.parametrize("fresnel", [False, True])
+def test_gs_error_reduction(n_levels, fresnel):
+    h_, w_ = 32, 40
+    a = synth.blur_target(h_, w_, 1.5, seed=21).astype(np.float64)
+    c = optics.chirp(h_, w_, LAM, PITCH, 0.02) if fresnel else None
+    phi0 = synth.uniform_phase(h_, w_, seed=22).astype(np.float64)
+    h, _ = project.slm_project(np.exp(1j * phi0), n_levels)
+    errs = [gs.replay_error(h, a, c)]
+    for _ in range(25):
+        h = gs.gs_step(h, a, n_levels, c)["h"]
+        errs.append(gs.replay_error(h, a, c))
+    e = np.array(errs)
+    assert np.all(e[1:] <= e[:-1] * (1 + 1e-12)), e
+    assert e[-1] < e[0]
+
+
+def test_gs_run_matches_step_chain_and_curve():
+    a = synth.blur_target(16, 24, 2.0, seed=3).astype(np.float64)
+    phi0 = synth.uniform_phase(16, 24, seed=4).astype(np.float64)
+    out = gs.gs(a, phi0, 6, n_levels=4)
+    h, _ = project.slm_project(np.exp(1j * phi0), 4)
+    from oracle.fft import fft2
+    from oracle.metrics import nmse
+    for k in range(6):
+        assert abs(out["nmse"][k] - nmse(np.abs(fft2(h)) ** 2, a * a)) < 1e-14
+        h = gs.gs_step(h, a, 4)["h"]
+    np.testing.assert_allclose(out["h"], h, atol=0)
+
+
+@pytest.mark.parametrize("n_levels", [0, 4])
+def test_gs_fixed_point(n_levels):
+    r = np.random.default_rng(31)
+    if n_levels:
+        hstar = project.level_field(r.integers(0, n_levels, (24, 16)), n_levels)
+    else:
+        hstar = np.exp(2j * np.pi * r.random((24, 16)))
+    from oracle.fft import fft2
+    a = np.abs(fft2(hstar))
+    out = gs.gs(a, project.phase_of(hstar), 5, n_levels=n_levels)
+    np.testing.assert_allclose(out["h"], hstar, atol=1e-12)
+    assert np.max(out["nmse"]) < 1e-24
+
+
+def test_gs_one_iteration_bruteforce_8x8():
+    a = synth.blur_target(8, 8, 1.0, seed=5).astype(np.float64)
+    phi0 = synth.uniform_phase(8, 8, seed=6).astype(np.float64)
+    h0 = np.exp(1j * phi0)
+    r = dft.dft2_bruteforce(h0)
+    a_s = a * np.sqrt(64 / np.sum(a * a))
+    rp = a_s * r / np.abs(r)
+    g = dft.dft2_bruteforce(rp, inverse=True)
+    want = g / np.abs(g)
+    np.testing.assert_allclose(gs.gs_step(h0, a, 0)["h"], want, atol=1e-13)
+
+
+# ------------------------------------------------------------------ multi-plane GS
+
+
+def test_multiplane_p1_equals_gs():
+    a = synth.spots_target(32, 32, 6, seed=41).astype(np.float64)
+    phi0 = synth.uniform_phase(32, 32, seed=42).astype(np.float64)
+    c = optics.chirp(32, 32, LAM, PITCH, 0.05)
+    m = gs.multiplane_gs([a], phi0, 5, [c], n_levels=0)
+    s = gs.gs(a, phi0, 5, n_levels=0, c=c)
+    np.testing.assert_allclose(m["h"], s["h"], atol=1e-12)
+    np.testing.assert_allclose(m["nmse"], s["nmse"], atol=1e-13)
+
+
+def test_multiplane_error_reduction():
+    n = 32
+    amps = [synth.spots_target(n, n, 6, seed=s).astype(np.float64) for s in (51, 52, 53)]
+    cs = [optics.chirp(n, n, LAM, PITCH, z) for z in (0.02, 0.03, 0.04)]
+    phi0 = synth.uniform_phase(n, n, seed=54).astype(np.float64)
+    h = np.exp(1j * phi0)
+    errs = [gs.multiplane_error(h, amps, cs)]
+    for _ in range(15):
+        h = gs.multiplane_gs(amps, project.phase_of(h), 1, cs)["h"]
+        errs.append(gs.multiplane_error(h, amps, cs))
+    e = np.array(errs)
+    assert np.all(e[1:] <= e[:-1] * (1 + 1e-12)), e
+
+
+# ------------------------------------------------------------------ Philox / OSPR
+
+
+def test_philox_known_answers():
+    with open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")) as f:
+        rows = [l.split() for l in f if l.strip() and not l.startswith("#")]
+    assert len(rows) == 3
+    for row in rows:
+        v = [int(x, 16) for x in row]
+        out = philox.philox4x32_10(tuple(v[0:4]), tuple(v[4:6]))
+        assert [int(o) for o in out] == v[6:10]
+
+
+def test_ospr_uniform_properties():
+    u = philox.ospr_uniform(1 << 16, 3, 2, 1234)
+    assert u.min() >= 0.0 and u.max() < 1.0
+    assert np.all(u * 2**24 == np.floor(u * 2**24))
+    assert abs(u.mean() - 0.5) < 0.01
+    # distinct subframes and targets give different draws
+    assert not np.array_equal(u, philox.ospr_uniform(1 << 16, 4, 2, 1234))
+    assert not np.array_equal(u, philox.ospr_uniform(1 << 16, 3, 3, 1234))
+
+
+def test_bit_pack_roundtrip():
+    q = np.random.default_rng(3).integers(0, 2, (7, 70))
+    w = ospr.pack_bits(q)
+    assert w.shape == (7, 3) and w.dtype == np.uint32
+    assert np.array_equal(ospr.unpack_bits(w, 70), q)
+    # LSB-first: pixel 0 is bit 0 of word 0
+    q1 = np.zeros((1, 40), dtype=np.int64)
+    q1[0, 0] = 1
+    q1[0, 33] = 1
+    assert list(ospr.pack_bits(q1)[0]) == [1, 2]
+
+
+def test_ospr_replay_is_hermitian():
+    a = synth.symmetrise(synth.blur_target(24, 30, 2.0, seed=61)).astype(np.float64)
+    sf = ospr.ospr_subframe(a, 0, 0, 77)
+    i = sf["intensity"]
+    i_neg = np.roll(i[::-1, ::-1], (1, 1), axis=(0, 1))
+    np.testing.assert_allclose(i, i_neg, rtol=1e-12, atol=1e-12 * i.max())
+    assert set(np.unique(sf["h"].real)) <= {-1.0, 1.0}
+
+
+def test_ospr_nmse_falls_with_subframes():
+    curves = []
+    for t in range(3):
+        a = synth.symmetrise(synth.blur_target(32, 32, 2.0, seed=70 + t)).astype(np.float64)
+        curves.append(ospr.ospr(a, 16, t, 3000)["nmse"])
+    c = np.mean(curves, axis=0)
+    assert c[15] < c[3] < c[0]
+
+
+def test_ospr_bits_match_levels():
+    a = synth.symmetrise(synth.blur_target(16, 40, 2.0, seed=81)).astype(np.float64)
+    out = ospr.ospr(a, 3, 1, 5, n_iter=2)
+    for s in range(3):
+        assert np.array_equal(ospr.unpack_bits(out["bits"][s], 40), out["q"][s])
+
+
+# ------------------------------------------------------------------ GD
+
+
+def _gd_problem(n=64, seed=90):
+    ts = [synth.spots_target(n, n, 8, seed=seed + p).astype(np.float64) ** 2 for p in range(3)]
+    ts = [t / np.sqrt(np.sum(t * t)) for t in ts]
+    cs = [optics.chirp(n, n, LAM, PITCH, z) for z in (0.08, 0.10, 0.12)]
+    phi = synth.uniform_phase(n, n, seed=seed + 9).astype(np.float64)
+    return phi, ts, cs
+
+
+def test_gd_gradient_finite_differences():
+    phi, ts, cs = _gd_problem()
+    _, _, g = gd.loss_and_grad(phi, ts, cs)
+    r = np.random.default_rng(5)
+    idx = r.choice(phi.size, 48, replace=False)
+    eps = 1e-6
+    fd = []
+    for k in idx:
+        e = np.zeros(phi.size)
+        e[k] = eps
+        e = e.reshape(phi.shape)
+        fd.append((gd.loss_only(phi + e, ts, cs) - gd.loss_only(phi - e, ts, cs)) / (2 * eps))
+    fd = np.array(fd)
+    assert np.linalg.norm(fd - g.ravel()[idx]) / np.linalg.norm(fd) < 1e-6
+    # directional derivative over all pixels at once
+    v = r.standard_normal(phi.shape)
+    t = 1e-6
+    dfd = (gd.loss_only(phi + t * v, ts, cs) - gd.loss_only(phi - t * v, ts, cs)) / (2 * t)
+    assert abs(dfd - np.sum(g * v)) / abs(dfd) < 1e-6
+
+
+def test_gd_gradient_vs_float64_autograd():
+    torch = pytest.importorskip("torch")
+    phi, ts, cs = _gd_problem(n=48, seed=95)
+    _, lp, g = gd.loss_and_grad(phi, ts, cs)
+    tp = torch.tensor(phi, dtype=torch.float64, requires_grad=True)
+    h = torch.exp(1j * tp.to(torch.complex128))
+    losses = []
+    for t, c in zip(ts, cs):
+        u = torch.fft.fft2(h * torch.tensor(c), norm="ortho")
+        i = u.real**2 + u.imag**2
+        tt = torch.tensor(t)
+        s = (i * tt).sum() / (i * i).sum()
+        s = s.detach()  # the optimal scale is held fixed (envelope theorem)
+        losses.append(((s * i - tt) ** 2).sum() / (tt * tt).sum())
+    loss = torch.stack(losses).mean()
+    loss.backward()
+    assert abs(loss.item() - np.mean(lp)) < 1e-12
+    np.testing.assert_allclose(tp.grad.numpy(), g, rtol=0, atol=1e-10 * np.abs(g).max())
+
+
+def test_adam_matches_torch():
+    torch = pytest.importorskip("torch")
+    r = np.random.default_rng(8)
+    phi = r.random((6, 5))
+    m = np.zeros_like(phi)
+    v = np.zeros_like(phi)
+    tp = torch.tensor(phi, dtype=torch.float64, requires_grad=True)
+    opt = torch.optim.Adam([tp], lr=0.05, betas=(0.9, 0.999), eps=1e-8)
+    for step in range(1, 6):
+        g = r.standard_normal(phi.shape)
+        phi, m, v = gd.adam_update(phi, g, m, v, step, 0.05)
+        opt.zero_grad()
+        tp.grad = torch.tensor(g)
+        opt.step()
+        np.testing.assert_allclose(tp.detach().numpy(), phi, rtol=0, atol=1e-14)
+
+
+def test_gd_decreases_loss():
+    phi, ts, cs = _gd_problem(n=32, seed=99)
+    out = gd.gd_run(phi, ts, cs, 30, 0.05)
+    assert out["loss"][-1] < 0.5 * out["loss"][0]
