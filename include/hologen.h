@@ -1,0 +1,142 @@
+/*
+ * hologen.h -- C ABI of the GB300 phase-retrieval library (libhologen.so).
+ *
+ * The paper (section "Algorithm Interface") passes a target image and the algorithm parameters down
+ * to a CUDA class (AlgorithmCuda: "stores target, illumination and starting images as well as
+ * common algorithm parameters"), whose RunIterations() runs the loop.  This header is that
+ * boundary, re-cut as a plan object plus one call per algorithm:
+ *
+ *   hg_plan_create / hg_plan_destroy   sizes, propagation (Fourier / Fresnel: wavelength, pitch,
+ *                                      distances) and quantisation levels; owns tables + workspace
+ *   hg_propagate                       bare forward / inverse Fourier or Fresnel transform
+ *   hg_gs_run                          Gerchberg-Saxton (section "Algorithm Libraries",
+ *                                      HoloGenAlgGSCuda), single- or multi-plane
+ *   hg_ospr_run                        One-Step Phase-Retrieval (HoloGenAlgOSPRCuda)
+ *   hg_gd_step                         one Adam step of gradient-descent hologram optimisation
+ *                                      (no counterpart in the paper)
+ *
+ * Conventions (every entry point):
+ *  - Data pointers are DEVICE pointers owned by the caller (CUDA global memory on the plan's device).
+ *    Arrays typed `T* const*` are HOST arrays holding one device pointer per item (n_items entries)
+ *    or per item and plane (item-major: [item * n_planes + plane]).
+ *  - Fields are complex64 stored as interleaved (re, im) float32, row-major [H][W], FFT order
+ *    (DC at [0][0]).  Real images are float32 [H][W] row-major.  Field pointers must be 8-byte
+ *    aligned, float pointers 4-byte aligned.
+ *  - Calls are asynchronous and stream-ordered on `stream` (a cudaStream_t; NULL = legacy default
+ *    stream).  Only hg_plan_create, hg_plan_destroy and hg_plan_sync synchronise the host.
+ *  - Each call returns a status and never throws.  Argument errors leave outputs untouched.  A CUDA
+ *    launch error is returned as HG_ERR_CUDA; asynchronous device errors surface on a later call or
+ *    in hg_plan_sync.  hg_last_error() gives a thread-local detail string for the last failure.
+ *  - Device pointers are checked before launch: a pointer that is not device memory of the plan's
+ *    device, or a buffer that does not fit in its allocation, is rejected with HG_ERR_INVALID_ARG.
+ *  - A plan is used from one host thread at a time.  Different plans are independent.
+ *  - Supported FFT lengths (H and W): 8, 16, 32, 64, 128, 256, 512, 1024, 2048, 4096, 12, 15, 30,
+ *    60, 120, 864, 1080, 1536, 1920.  Other sizes give HG_ERR_UNSUPPORTED_SIZE.
+ */
+#ifndef HOLOGEN_H
+#define HOLOGEN_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define HG_API __attribute__((visibility("default")))
+#else
+#define HG_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HG_OK = 0,
+  HG_ERR_INVALID_ARG = 1,
+  HG_ERR_UNSUPPORTED_SIZE = 2,
+  HG_ERR_OUT_OF_MEMORY = 3,
+  HG_ERR_CUDA = 4,
+  HG_ERR_TIMEOUT = 5,
+  HG_ERR_INTERNAL = 6
+} hg_status;
+
+/* Fourier / Fresnel holograms (paper keywords "Fourier", "Fresnel"). */
+typedef enum { HG_FOURIER = 0, HG_FRESNEL = 1 } hg_propagation;
+
+typedef struct hg_plan hg_plan;
+
+typedef struct {
+  int32_t n_items;         /* holograms per run, 1..256 */
+  const int32_t* heights;  /* H of each item (n_items entries) */
+  const int32_t* widths;   /* W of each item */
+  int32_t propagation;     /* hg_propagation */
+  double wavelength_m;     /* Fresnel: wavelength lambda (> 0) */
+  double pitch_m;          /* Fresnel: SLM pixel pitch p (> 0) */
+  int32_t n_planes;        /* replay planes P >= 1 (Fourier: must be 1) */
+  const double* z_m;       /* Fresnel: P propagation distances (> 0); may be NULL for Fourier */
+  int32_t quant_levels;    /* 0 continuous phase; 2 binary {0, pi}; N in 3..256 N-level */
+  uint32_t flags;          /* reserved, must be 0 */
+} hg_plan_desc;
+
+/*
+ * Fresnel model (single-FFT, reading of the paper's "Fresnel" keyword): SLM pixel (i, j) at
+ * y_i = (i - floor(H/2)) p, x_j = (j - floor(W/2)) p; input chirp
+ * c(i, j) = exp(i pi (x_j^2 + y_i^2) / (lambda z)); forward R = F(h c), inverse g = conj(c) F^-1(R).
+ * F is the unitary 2D DFT.  The output-plane chirp and constant phase factor are omitted.
+ *
+ * SLM projection: continuous h = g/|g| (1 where g = 0); N-level: nearest of exp(2 pi i q / N),
+ * q = floor(arg(g) N / (2 pi) + 1/2) mod N, arg in [0, 2 pi).
+ */
+
+/* Creates a plan on the current CUDA device.  desc (and its arrays) may be freed after the call.
+ * Errors: INVALID_ARG (bad field), UNSUPPORTED_SIZE (H or W not a supported length),
+ * OUT_OF_MEMORY (workspace), CUDA. */
+HG_API hg_status hg_plan_create(const hg_plan_desc* desc, hg_plan** out);
+
+/* Destroys a plan (synchronises its device first).  NULL is accepted. */
+HG_API hg_status hg_plan_destroy(hg_plan* plan);
+
+/* Waits for all work issued by the plan and reports any asynchronous device error. */
+HG_API hg_status hg_plan_sync(hg_plan* plan);
+
+/*
+ * Bare propagation of every item through plane `plane` (0..P-1):
+ *   direction +1:  out = F(in * c)          direction -1:  out = conj(c) * F^-1(in)
+ * (c = 1 for Fourier).  in[k], out[k]: complex64 [H_k][W_k]; in and out may alias (in place).
+ */
+HG_API hg_status hg_propagate(hg_plan* plan, int32_t plane, int32_t direction, const void* const* in,
+                       void* const* out, void* stream);
+
+/*
+ * Gerchberg-Saxton phase retrieval (Gerchberg & Saxton 1972, error-reduction form), n_iter >= 0
+ * iterations for every item:
+ *   h_0 = P_SLM(exp(i phi_0));  R_k = F(h_k c);  R'_k = A R_k / |R_k|;
+ *   h_{k+1} = P_SLM(conj(c) F^-1(R'_k)).
+ * With P > 1 planes the SLM update averages the P back-propagated fields (multi-plane GS,
+ * averaged projections) before projecting.
+ *  target_amp[k*P + p]  float32 [H][W] target amplitude A of item k, plane p (FFT order, >= 0)
+ *  init_phase           NULL, or per item NULL / float32 [H][W] starting phase phi_0 (radians);
+ *                       a NULL entry draws phi_0 = 2 pi u, u from Philox4x32-10 with counter
+ *                       (pixel, 0, 1, 0) and key (seed_lo, seed_hi ^ item)
+ *  phase_out            NULL, or per item NULL / float32 [H][W]: phase of h_{n_iter} in [0, 2 pi)
+ *  level_out            NULL, or per item NULL / uint8 [H][W]: level index q (quantised plans only)
+ *  nmse_out             NULL or device float32 [n_items][n_iter + 1]: NMSE of h_k, k = 0..n_iter,
+ *                       NMSE = 1 - (sum I T)^2 / (sum I^2 sum T^2), I = |R|^2, T = A^2 (mean over
+ *                       planes when P > 1)
+ */
+HG_API hg_status hg_gs_run(hg_plan* plan, const float* const* target_amp, const float* const* init_phase,
+                    uint64_t seed, int32_t n_iter, float* const* phase_out, uint8_t* const* level_out,
+                    float* nmse_out, void* stream);
+
+/* Human-readable name of a status code (static string). */
+HG_API const char* hg_status_string(hg_status status);
+
+/* Detail message of the last failing call on this host thread ("" if none). */
+HG_API const char* hg_last_error(void);
+
+/* 1 if n is a supported FFT length, else 0. */
+HG_API int32_t hg_supported_length(int32_t n);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HOLOGEN_H */

@@ -52,3 +52,14 @@ def ospr_uniform(n_pixels: int, subframe: int, target: int, seed: int) -> np.nda
     k1 = ((seed >> 32) ^ int(target)) & 0xFFFFFFFF
     x0, _, _, _ = philox4x32_10((p, subframe, 0, 0), (k0, k1))
     return (x0 >> np.uint32(8)).astype(np.float64) * (2.0 ** -24)
+
+
+def init_uniform(n_pixels: int, item: int, seed: int) -> np.ndarray:
+    """Starting-phase draws u for pixels p = 0..n-1: word 0 of Philox4x32-10 with counter
+    (p, 0, 1, 0) and key (seed_lo, seed_hi ^ item), u = (x >> 8) 2^-24.  phi_0 = 2 pi u."""
+    p = np.arange(n_pixels, dtype=np.uint64)
+    seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+    k0 = seed & 0xFFFFFFFF
+    k1 = ((seed >> 32) ^ int(item)) & 0xFFFFFFFF
+    x0, _, _, _ = philox4x32_10((p, 0, 1, 0), (k0, k1))
+    return (x0 >> np.uint32(8)).astype(np.float64) * (2.0 ** -24)

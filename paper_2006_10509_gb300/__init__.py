@@ -1,0 +1,216 @@
+"""Python binding of libhologen (GB300 phase-retrieval library) -- ctypes over the C ABI.
+
+The functions below carry the C names (``hg_plan_create``, ``hg_propagate``, ``hg_gs_run`` ...) and
+only marshal arguments: torch tensors become device pointers, the current torch stream becomes the
+``cudaStream_t``, and a non-OK status becomes :class:`HologenError`.  Every step of the computation
+runs in the library's CUDA kernels; there is no fallback path.  The library is built in-tree by
+``paper_2006_10509_gb300.build.build()``; importing this package does not load it, the first call
+does, and fails loudly if it has not been built.
+
+Layout conventions follow ``include/hologen.h``: complex64 [H][W] fields (torch.complex64), float32
+[H][W] images, FFT order (DC at [0][0]).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Sequence
+
+__all__ = [
+    "HG_OK", "HG_ERR_INVALID_ARG", "HG_ERR_UNSUPPORTED_SIZE", "HG_ERR_OUT_OF_MEMORY", "HG_ERR_CUDA",
+    "HG_ERR_TIMEOUT", "HG_ERR_INTERNAL", "HG_FOURIER", "HG_FRESNEL",
+    "HologenError", "lib_path", "load", "hg_plan_create", "hg_plan_destroy", "hg_plan_sync",
+    "hg_propagate", "hg_gs_run", "hg_status_string", "hg_last_error", "hg_supported_length", "Plan",
+]
+
+HG_OK, HG_ERR_INVALID_ARG, HG_ERR_UNSUPPORTED_SIZE, HG_ERR_OUT_OF_MEMORY = 0, 1, 2, 3
+HG_ERR_CUDA, HG_ERR_TIMEOUT, HG_ERR_INTERNAL = 4, 5, 6
+HG_FOURIER, HG_FRESNEL = 0, 1
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB = None
+
+
+def lib_path() -> str:
+    return os.path.join(_HERE, "libhologen.so")
+
+
+class hg_plan_desc(ctypes.Structure):
+    _fields_ = [
+        ("n_items", ctypes.c_int32),
+        ("heights", ctypes.POINTER(ctypes.c_int32)),
+        ("widths", ctypes.POINTER(ctypes.c_int32)),
+        ("propagation", ctypes.c_int32),
+        ("wavelength_m", ctypes.c_double),
+        ("pitch_m", ctypes.c_double),
+        ("n_planes", ctypes.c_int32),
+        ("z_m", ctypes.POINTER(ctypes.c_double)),
+        ("quant_levels", ctypes.c_int32),
+        ("flags", ctypes.c_uint32),
+    ]
+
+
+class HologenError(RuntimeError):
+    def __init__(self, status: int, func: str, detail: str):
+        self.status = status
+        super().__init__(f"{func}: {_status_name(status)}: {detail}")
+
+
+_VP = ctypes.c_void_p
+_PP = ctypes.POINTER(ctypes.c_void_p)
+
+_SIGNATURES = {
+    "hg_plan_create": (ctypes.c_int, [ctypes.POINTER(hg_plan_desc), ctypes.POINTER(ctypes.c_void_p)]),
+    "hg_plan_destroy": (ctypes.c_int, [_VP]),
+    "hg_plan_sync": (ctypes.c_int, [_VP]),
+    "hg_propagate": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32, _PP, _PP, _VP]),
+    "hg_gs_run": (ctypes.c_int, [_VP, _PP, _PP, ctypes.c_uint64, ctypes.c_int32, _PP, _PP, _VP, _VP]),
+    "hg_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "hg_last_error": (ctypes.c_char_p, []),
+    "hg_supported_length": (ctypes.c_int32, [ctypes.c_int32]),
+}
+
+
+def load():
+    """Loads libhologen.so (once).  Raises RuntimeError if it has not been built."""
+    global _LIB
+    if _LIB is None:
+        path = lib_path()
+        if not os.path.exists(path):
+            raise RuntimeError(
+                f"{path} is missing: build it with `python -m paper_2006_10509_gb300.build` "
+                "(the CUDA library is required; there is no CPU fallback)")
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in _SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _LIB = lib
+    return _LIB
+
+
+def _status_name(s: int) -> str:
+    try:
+        return load().hg_status_string(s).decode()
+    except Exception:  # noqa: BLE001 - naming a status must never raise
+        return f"status {s}"
+
+
+def _check(status: int, func: str):
+    if status != HG_OK:
+        raise HologenError(status, func, load().hg_last_error().decode())
+
+
+def _ptr_array(items) -> ctypes.Array | None:
+    """Host array of device pointers from a sequence of tensors / None (None stays NULL)."""
+    if items is None:
+        return None
+    arr = (ctypes.c_void_p * len(items))()
+    for i, t in enumerate(items):
+        arr[i] = None if t is None else _data_ptr(t)
+    return arr
+
+
+def _data_ptr(t) -> int:
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        import torch
+
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def hg_status_string(status: int) -> str:
+    return load().hg_status_string(status).decode()
+
+
+def hg_last_error() -> str:
+    return load().hg_last_error().decode()
+
+
+def hg_supported_length(n: int) -> bool:
+    return bool(load().hg_supported_length(n))
+
+
+def hg_plan_create(heights: Sequence[int], widths: Sequence[int], propagation: int = HG_FOURIER,
+                   wavelength_m: float = 0.0, pitch_m: float = 0.0, z_m: Sequence[float] | None = None,
+                   quant_levels: int = 0, flags: int = 0) -> int:
+    """Creates a plan on the current device; returns the opaque handle (int)."""
+    n = len(heights)
+    hs = (ctypes.c_int32 * n)(*heights)
+    ws = (ctypes.c_int32 * len(widths))(*widths)
+    zs = (ctypes.c_double * len(z_m))(*z_m) if z_m else None
+    d = hg_plan_desc(n, hs, ws, propagation, wavelength_m, pitch_m, len(z_m) if z_m else 1, zs,
+                     quant_levels, flags)
+    out = ctypes.c_void_p()
+    _check(load().hg_plan_create(ctypes.byref(d), ctypes.byref(out)), "hg_plan_create")
+    return out.value
+
+
+def hg_plan_destroy(plan: int | None):
+    _check(load().hg_plan_destroy(plan), "hg_plan_destroy")
+
+
+def hg_plan_sync(plan: int):
+    _check(load().hg_plan_sync(plan), "hg_plan_sync")
+
+
+def hg_propagate(plan: int, plane: int, direction: int, inputs, outputs, stream=None):
+    """out_k = F(in_k c) (direction +1) or conj(c) F^-1(in_k) (direction -1) for every item."""
+    _check(load().hg_propagate(plan, plane, direction, _ptr_array(inputs), _ptr_array(outputs), _stream(stream)),
+           "hg_propagate")
+
+
+def hg_gs_run(plan: int, target_amp, init_phase=None, seed: int = 0, n_iter: int = 1, phase_out=None,
+              level_out=None, nmse_out=None, stream=None):
+    """Gerchberg-Saxton for every item of the plan (see hologen.h for the argument layout)."""
+    _check(load().hg_gs_run(plan, _ptr_array(target_amp), _ptr_array(init_phase), seed, n_iter,
+                            _ptr_array(phase_out), _ptr_array(level_out),
+                            None if nmse_out is None else _data_ptr(nmse_out), _stream(stream)), "hg_gs_run")
+
+
+class Plan:
+    """Owning wrapper around a plan handle (destroyed on close / exit / garbage collection)."""
+
+    def __init__(self, heights, widths, propagation=HG_FOURIER, wavelength_m=0.0, pitch_m=0.0, z_m=None,
+                 quant_levels=0):
+        self.heights = list(heights)
+        self.widths = list(widths)
+        self.n_planes = len(z_m) if z_m else 1
+        self.quant_levels = quant_levels
+        self.handle = hg_plan_create(self.heights, self.widths, propagation, wavelength_m, pitch_m, z_m,
+                                     quant_levels)
+
+    def close(self):
+        if self.handle is not None:
+            hg_plan_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001 - never raise from a finaliser
+            pass
+
+    def propagate(self, inputs, outputs, direction=1, plane=0, stream=None):
+        hg_propagate(self.handle, plane, direction, inputs, outputs, stream)
+
+    def gs(self, target_amp, n_iter, init_phase=None, seed=0, phase_out=None, level_out=None, nmse_out=None,
+           stream=None):
+        hg_gs_run(self.handle, target_amp, init_phase, seed, n_iter, phase_out, level_out, nmse_out, stream)
+
+    def sync(self):
+        hg_plan_sync(self.handle)

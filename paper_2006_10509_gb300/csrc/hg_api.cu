@@ -1,0 +1,500 @@
+// C ABI of libhologen: plan objects, argument validation and the launch sequences of each call.
+//
+// Role of the paper's AlgorithmCuda base class (section "Algorithm Libraries": it keeps the target,
+// illumination and starting images and common parameters, and handles device transfer): here the
+// caller owns the images in device memory and the plan owns everything derived from the parameters
+// (twiddle, chirp and level tables; the field workspace; reduction scratch).
+#include <dlfcn.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/hologen.h"
+#include "hg_kernels.cuh"
+#include "hg_launch.h"
+
+namespace hg {
+
+const RowKernels* row_kernels(int n) {
+  switch (n) {
+#define HG_CASE(N) \
+  case N:          \
+    return &row_kernels_##N();
+    HG_FOR_EACH_LENGTH(HG_CASE)
+#undef HG_CASE
+    default:
+      return nullptr;
+  }
+}
+
+const ColKernels* col_kernels(int n) {
+  switch (n) {
+#define HG_CASE(N) \
+  case N:          \
+    return &col_kernels_##N();
+    HG_FOR_EACH_LENGTH(HG_CASE)
+#undef HG_CASE
+    default:
+      return nullptr;
+  }
+}
+
+}  // namespace hg
+
+namespace {
+
+thread_local std::string g_err;
+
+hg_status fail(hg_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+
+hg_status cuda_fail(cudaError_t e, const char* what) {
+  cudaGetLastError();
+  if (e == cudaErrorMemoryAllocation) return fail(HG_ERR_OUT_OF_MEMORY, "%s: %s", what, cudaGetErrorString(e));
+  return fail(HG_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define HG_CUDA(call, what)                         \
+  do {                                              \
+    cudaError_t e_ = (call);                        \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+  } while (0)
+
+// cuMemGetAddressRange_v2 from the driver, found at run time (the library does not link libcuda).
+typedef int (*range_fn_t)(unsigned long long*, size_t*, unsigned long long);
+range_fn_t range_fn() {
+  static range_fn_t fn = [] {
+    void* h = dlopen("libcuda.so.1", RTLD_NOW | RTLD_LOCAL);
+    return h ? (range_fn_t)dlsym(h, "cuMemGetAddressRange_v2") : (range_fn_t) nullptr;
+  }();
+  return fn;
+}
+
+constexpr int kMaxItems = 256;
+constexpr int kMaxLevels = 256;
+
+struct SizeClass {
+  int H = 0, W = 0;
+  std::vector<int> items;  // plan item indices, in order; slot = position
+  const hg::RowKernels* rk = nullptr;
+  const hg::ColKernels* ck = nullptr;
+  float2* field = nullptr;       // [slot][plane][H][W]
+  double* partials = nullptr;    // [slot][plane][3 * col_blocks]
+  unsigned* counters = nullptr;  // [slot][plane]
+  std::vector<float2*> cx, cy;   // per plane (Fresnel)
+  int row_blocks() const { return (H + rk->rows - 1) / rk->rows; }
+  int col_blocks() const { return (W + ck->cols - 1) / ck->cols; }
+};
+
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) {
+      ok = false;
+      return;
+    }
+    if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+  }
+  ~DeviceGuard() {
+    int cur;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+}  // namespace
+
+struct hg_plan {
+  int device = 0;
+  int n_items = 0;
+  std::vector<int> H, W;
+  int propagation = HG_FOURIER;
+  double lambda = 0, pitch = 0;
+  int P = 1;
+  std::vector<double> z;
+  int levels = 0;
+  std::vector<SizeClass> classes;
+  std::vector<int> item_class, item_slot;
+  std::map<int, float2*> tw;
+  float2* lev = nullptr;
+  float* lev_phase = nullptr;
+  std::vector<void*> allocs;
+
+  ~hg_plan() {
+    for (void* p : allocs) cudaFree(p);
+  }
+  template <class T>
+  hg_status alloc(T** p, size_t count, const char* what) {
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, count * sizeof(T) > 0 ? count * sizeof(T) : 16);
+    if (e != cudaSuccess) return cuda_fail(e, what);
+    allocs.push_back(q);
+    *p = (T*)q;
+    return HG_OK;
+  }
+};
+
+namespace {
+
+// Device pointer check: device (or managed) memory of the plan's device, aligned, and -- where the
+// driver can tell -- [ptr, ptr + bytes) inside one allocation.
+hg_status check_ptr(const hg_plan* p, const void* ptr, size_t bytes, size_t align, const char* what, int idx) {
+  if (!ptr) return fail(HG_ERR_INVALID_ARG, "%s[%d] is NULL", what, idx);
+  if ((uintptr_t)ptr % align) return fail(HG_ERR_INVALID_ARG, "%s[%d] is not %zu-byte aligned", what, idx, align);
+  cudaPointerAttributes at;
+  cudaError_t e = cudaPointerGetAttributes(&at, ptr);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(HG_ERR_INVALID_ARG, "%s[%d] is not a CUDA pointer (%s)", what, idx, cudaGetErrorString(e));
+  }
+  if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)
+    return fail(HG_ERR_INVALID_ARG, "%s[%d] is not device memory", what, idx);
+  if (at.type == cudaMemoryTypeDevice && at.device != p->device)
+    return fail(HG_ERR_INVALID_ARG, "%s[%d] lives on device %d, plan is on device %d", what, idx, at.device, p->device);
+  if (range_fn_t fn = range_fn()) {
+    unsigned long long base = 0;
+    size_t size = 0;
+    if (fn(&base, &size, (unsigned long long)(uintptr_t)ptr) == 0) {
+      if ((unsigned long long)(uintptr_t)ptr + bytes > base + size)
+        return fail(HG_ERR_INVALID_ARG, "%s[%d]: %zu bytes do not fit in its allocation", what, idx, bytes);
+    }
+  }
+  return HG_OK;
+}
+
+hg_status launch(const void* fn, dim3 grid, int nt, int smem, const hg::PassArgs& a, cudaStream_t s) {
+  void* args[] = {(void*)&a};
+  cudaError_t e = cudaLaunchKernel(fn, grid, dim3(nt), args, (size_t)smem, s);
+  if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+  return HG_OK;
+}
+
+// twiddles exp(-2 pi i t / n), t < n, in float64 then rounded
+std::vector<float2> twiddles(int n) {
+  std::vector<float2> t(n);
+  const double two_pi = 6.283185307179586476925286766559;
+  for (int i = 0; i < n; ++i) {
+    const double a = two_pi * (double)i / (double)n;
+    t[i] = make_float2((float)std::cos(a), (float)-std::sin(a));
+  }
+  return t;
+}
+
+// chirp factor exp(i pi (d p)^2 / (lambda z)), d = index - floor(n/2); the phase is reduced in turns
+// (fractional part of (d p)^2 / (2 lambda z)) in float64 before the trig call
+std::vector<float2> chirp_axis(int n, double pitch, double lambda, double z) {
+  std::vector<float2> c(n);
+  const double two_pi = 6.283185307179586476925286766559;
+  for (int i = 0; i < n; ++i) {
+    const double d = (double)(i - n / 2) * pitch;
+    double turns = d * d / (2.0 * lambda * z);
+    turns -= std::floor(turns);
+    c[i] = make_float2((float)std::cos(two_pi * turns), (float)std::sin(two_pi * turns));
+  }
+  return c;
+}
+
+template <class T>
+hg_status upload(hg_plan* p, T** dst, const std::vector<T>& v, const char* what) {
+  hg_status s = p->alloc(dst, v.size(), what);
+  if (s != HG_OK) return s;
+  HG_CUDA(cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice), what);
+  return HG_OK;
+}
+
+void fill_common(const hg_plan* p, const SizeClass& c, int plane, hg::PassArgs& a) {
+  a.H = c.H;
+  a.W = c.W;
+  a.n_levels = p->levels;
+  a.tw_row = p->tw.at(c.W);
+  a.tw_col = p->tw.at(c.H);
+  a.cx = p->propagation == HG_FRESNEL ? c.cx[plane] : nullptr;
+  a.cy = p->propagation == HG_FRESNEL ? c.cy[plane] : nullptr;
+  a.lev = p->lev;
+  a.lev_phase = p->lev_phase;
+  a.field = c.field;
+  a.partials = c.partials;
+  a.counters = c.counters;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* hg_status_string(hg_status s) {
+  switch (s) {
+    case HG_OK: return "HG_OK";
+    case HG_ERR_INVALID_ARG: return "HG_ERR_INVALID_ARG";
+    case HG_ERR_UNSUPPORTED_SIZE: return "HG_ERR_UNSUPPORTED_SIZE";
+    case HG_ERR_OUT_OF_MEMORY: return "HG_ERR_OUT_OF_MEMORY";
+    case HG_ERR_CUDA: return "HG_ERR_CUDA";
+    case HG_ERR_TIMEOUT: return "HG_ERR_TIMEOUT";
+    case HG_ERR_INTERNAL: return "HG_ERR_INTERNAL";
+  }
+  return "HG_ERR_UNKNOWN";
+}
+
+const char* hg_last_error(void) { return g_err.c_str(); }
+
+int32_t hg_supported_length(int32_t n) { return hg::row_kernels(n) != nullptr && hg::col_kernels(n) != nullptr; }
+
+hg_status hg_plan_create(const hg_plan_desc* d, hg_plan** out) {
+  if (!out) return fail(HG_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!d) return fail(HG_ERR_INVALID_ARG, "desc is NULL");
+  if (d->n_items < 1 || d->n_items > kMaxItems) return fail(HG_ERR_INVALID_ARG, "n_items must be 1..%d", kMaxItems);
+  if (!d->heights || !d->widths) return fail(HG_ERR_INVALID_ARG, "heights / widths is NULL");
+  if (d->propagation != HG_FOURIER && d->propagation != HG_FRESNEL)
+    return fail(HG_ERR_INVALID_ARG, "unknown propagation %d", d->propagation);
+  if (d->n_planes < 1 || d->n_planes > 16) return fail(HG_ERR_INVALID_ARG, "n_planes must be 1..16");
+  if (d->propagation == HG_FOURIER && d->n_planes != 1)
+    return fail(HG_ERR_INVALID_ARG, "Fourier plans have exactly one plane");
+  if (d->quant_levels < 0 || d->quant_levels == 1 || d->quant_levels > kMaxLevels)
+    return fail(HG_ERR_INVALID_ARG, "quant_levels must be 0 or 2..%d", kMaxLevels);
+  if (d->flags != 0) return fail(HG_ERR_INVALID_ARG, "flags must be 0");
+  if (d->propagation == HG_FRESNEL) {
+    if (!(d->wavelength_m > 0) || !(d->pitch_m > 0) || !std::isfinite(d->wavelength_m) || !std::isfinite(d->pitch_m))
+      return fail(HG_ERR_INVALID_ARG, "Fresnel plans need wavelength_m > 0 and pitch_m > 0");
+    if (!d->z_m) return fail(HG_ERR_INVALID_ARG, "z_m is NULL");
+    for (int i = 0; i < d->n_planes; ++i)
+      if (!(d->z_m[i] > 0) || !std::isfinite(d->z_m[i])) return fail(HG_ERR_INVALID_ARG, "z_m[%d] must be > 0", i);
+  }
+  for (int i = 0; i < d->n_items; ++i) {
+    const int h = d->heights[i], w = d->widths[i];
+    if (h < 1 || w < 1) return fail(HG_ERR_INVALID_ARG, "item %d: size %dx%d", i, h, w);
+    if (!hg_supported_length(h) || !hg_supported_length(w))
+      return fail(HG_ERR_UNSUPPORTED_SIZE, "item %d: %dx%d is not a supported size", i, h, w);
+  }
+
+  hg_plan* p = new (std::nothrow) hg_plan();
+  if (!p) return fail(HG_ERR_OUT_OF_MEMORY, "host allocation");
+  auto bail = [&](hg_status s) {
+    delete p;
+    return s;
+  };
+  if (cudaGetDevice(&p->device) != cudaSuccess) {
+    cudaGetLastError();
+    return bail(fail(HG_ERR_CUDA, "no CUDA device"));
+  }
+  p->n_items = d->n_items;
+  p->H.assign(d->heights, d->heights + d->n_items);
+  p->W.assign(d->widths, d->widths + d->n_items);
+  p->propagation = d->propagation;
+  p->lambda = d->wavelength_m;
+  p->pitch = d->pitch_m;
+  p->P = d->n_planes;
+  if (d->propagation == HG_FRESNEL) p->z.assign(d->z_m, d->z_m + d->n_planes);
+  p->levels = d->quant_levels;
+
+  // size classes
+  p->item_class.resize(p->n_items);
+  p->item_slot.resize(p->n_items);
+  for (int i = 0; i < p->n_items; ++i) {
+    int ci = -1;
+    for (size_t c = 0; c < p->classes.size(); ++c)
+      if (p->classes[c].H == p->H[i] && p->classes[c].W == p->W[i]) ci = (int)c;
+    if (ci < 0) {
+      SizeClass c;
+      c.H = p->H[i];
+      c.W = p->W[i];
+      c.rk = hg::row_kernels(c.W);
+      c.ck = hg::col_kernels(c.H);
+      p->classes.push_back(c);
+      ci = (int)p->classes.size() - 1;
+    }
+    p->item_class[i] = ci;
+    p->item_slot[i] = (int)p->classes[ci].items.size();
+    p->classes[ci].items.push_back(i);
+  }
+
+  hg_status s;
+  for (SizeClass& c : p->classes) {
+    c.rk->set_attrs();
+    c.ck->set_attrs();
+    const size_t n = c.items.size() * (size_t)p->P;
+    if ((s = p->alloc(&c.field, n * c.H * c.W, "field workspace")) != HG_OK) return bail(s);
+    if ((s = p->alloc(&c.partials, n * 3 * c.col_blocks(), "reduction scratch")) != HG_OK) return bail(s);
+    if ((s = p->alloc(&c.counters, n, "reduction counters")) != HG_OK) return bail(s);
+    if (cudaMemset(c.counters, 0, n * sizeof(unsigned)) != cudaSuccess) return bail(cuda_fail(cudaGetLastError(), "memset"));
+    for (int pl = 0; pl < p->P; ++pl) {
+      float2 *cx = nullptr, *cy = nullptr;
+      if (p->propagation == HG_FRESNEL) {
+        if ((s = upload(p, &cx, chirp_axis(c.W, p->pitch, p->lambda, p->z[pl]), "chirp table")) != HG_OK) return bail(s);
+        if ((s = upload(p, &cy, chirp_axis(c.H, p->pitch, p->lambda, p->z[pl]), "chirp table")) != HG_OK) return bail(s);
+      }
+      c.cx.push_back(cx);
+      c.cy.push_back(cy);
+    }
+    for (int len : {c.H, c.W}) {
+      if (p->tw.count(len)) continue;
+      float2* t = nullptr;
+      if ((s = upload(p, &t, twiddles(len), "twiddle table")) != HG_OK) return bail(s);
+      p->tw[len] = t;
+    }
+  }
+  // level tables exp(2 pi i q / N) and 2 pi q / N, exact on the axes
+  {
+    const int nl = p->levels > 0 ? p->levels : 1;
+    std::vector<float2> lev(nl);
+    std::vector<float> ph(nl);
+    const double two_pi = 6.283185307179586476925286766559;
+    for (int q = 0; q < nl; ++q) {
+      const double a = two_pi * (double)q / (double)nl;
+      lev[q] = make_float2((float)std::cos(a), (float)std::sin(a));
+      if ((4 * q) % nl == 0) {
+        const int quarter = (4 * q / nl) % 4;
+        const float ax[4][2] = {{1.f, 0.f}, {0.f, 1.f}, {-1.f, 0.f}, {0.f, -1.f}};
+        lev[q] = make_float2(ax[quarter][0], ax[quarter][1]);
+      }
+      ph[q] = (float)a;
+    }
+    if ((s = upload(p, &p->lev, lev, "level table")) != HG_OK) return bail(s);
+    if ((s = upload(p, &p->lev_phase, ph, "level table")) != HG_OK) return bail(s);
+  }
+  if (cudaDeviceSynchronize() != cudaSuccess) return bail(cuda_fail(cudaGetLastError(), "plan set-up"));
+  *out = p;
+  return HG_OK;
+}
+
+hg_status hg_plan_destroy(hg_plan* p) {
+  if (!p) return HG_OK;
+  DeviceGuard g(p->device);
+  cudaDeviceSynchronize();
+  cudaGetLastError();
+  delete p;
+  return HG_OK;
+}
+
+hg_status hg_plan_sync(hg_plan* p) {
+  if (!p) return fail(HG_ERR_INVALID_ARG, "plan is NULL");
+  DeviceGuard g(p->device);
+  if (!g.ok) return fail(HG_ERR_CUDA, "cannot select device %d", p->device);
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(e, "device error");
+  return HG_OK;
+}
+
+hg_status hg_propagate(hg_plan* p, int32_t plane, int32_t direction, const void* const* in, void* const* out,
+                       void* stream) {
+  if (!p) return fail(HG_ERR_INVALID_ARG, "plan is NULL");
+  if (plane < 0 || plane >= p->P) return fail(HG_ERR_INVALID_ARG, "plane %d out of range", plane);
+  if (direction != 1 && direction != -1) return fail(HG_ERR_INVALID_ARG, "direction must be +1 or -1");
+  if (!in || !out) return fail(HG_ERR_INVALID_ARG, "in / out is NULL");
+  DeviceGuard g(p->device);
+  if (!g.ok) return fail(HG_ERR_CUDA, "cannot select device %d", p->device);
+  hg_status s;
+  for (int i = 0; i < p->n_items; ++i) {
+    const size_t bytes = (size_t)p->H[i] * p->W[i] * 8;
+    if ((s = check_ptr(p, in[i], bytes, 8, "in", i)) != HG_OK) return s;
+    if ((s = check_ptr(p, out[i], bytes, 8, "out", i)) != HG_OK) return s;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool inv = direction < 0;
+  const bool fres = p->propagation == HG_FRESNEL;
+  for (const SizeClass& c : p->classes) {
+    for (size_t c0 = 0; c0 < c.items.size(); c0 += hg::kMaxBatch) {
+      const int nb = (int)std::min<size_t>(hg::kMaxBatch, c.items.size() - c0);
+      hg::PassArgs a{};
+      fill_common(p, c, plane, a);
+      a.n_items = nb;
+      a.scale = (float)(1.0 / std::sqrt((double)c.H * (double)c.W));
+      for (int k = 0; k < nb; ++k) {
+        const int item = c.items[c0 + k];
+        a.item_index[k] = item;
+        a.class_slot[k] = (int)(c0 + k);
+        a.in[k] = (const float2*)in[item];
+        a.out[k] = (float2*)out[item];
+      }
+      if ((s = launch(c.rk->fft[inv][fres && !inv], dim3(c.row_blocks(), nb), c.rk->nt, c.rk->smem, a, st)) != HG_OK)
+        return s;
+      if ((s = launch(c.ck->fft[inv][fres && inv], dim3(c.col_blocks(), nb), c.ck->nt, c.ck->smem, a, st)) != HG_OK)
+        return s;
+    }
+  }
+  return HG_OK;
+}
+
+hg_status hg_gs_run(hg_plan* p, const float* const* target_amp, const float* const* init_phase, uint64_t seed,
+                    int32_t n_iter, float* const* phase_out, uint8_t* const* level_out, float* nmse_out,
+                    void* stream) {
+  if (!p) return fail(HG_ERR_INVALID_ARG, "plan is NULL");
+  if (n_iter < 0 || n_iter > 1000000) return fail(HG_ERR_INVALID_ARG, "n_iter must be 0..1000000");
+  if (!target_amp) return fail(HG_ERR_INVALID_ARG, "target_amp is NULL");
+  if (p->P != 1) return fail(HG_ERR_INVALID_ARG, "multi-plane GS is not available in this build");
+  if (level_out && p->levels == 0) {
+    for (int i = 0; i < p->n_items; ++i)
+      if (level_out[i]) return fail(HG_ERR_INVALID_ARG, "level_out needs a quantised plan");
+  }
+  DeviceGuard g(p->device);
+  if (!g.ok) return fail(HG_ERR_CUDA, "cannot select device %d", p->device);
+  hg_status s;
+  for (int i = 0; i < p->n_items; ++i) {
+    const size_t px = (size_t)p->H[i] * p->W[i];
+    if ((s = check_ptr(p, target_amp[i], px * 4, 4, "target_amp", i)) != HG_OK) return s;
+    if (init_phase && init_phase[i] && (s = check_ptr(p, init_phase[i], px * 4, 4, "init_phase", i)) != HG_OK)
+      return s;
+    if (phase_out && phase_out[i] && (s = check_ptr(p, phase_out[i], px * 4, 4, "phase_out", i)) != HG_OK) return s;
+    if (level_out && level_out[i] && (s = check_ptr(p, level_out[i], px, 1, "level_out", i)) != HG_OK) return s;
+  }
+  if (nmse_out && (s = check_ptr(p, nmse_out, (size_t)p->n_items * (n_iter + 1) * 4, 4, "nmse_out", 0)) != HG_OK)
+    return s;
+
+  cudaStream_t st = (cudaStream_t)stream;
+  for (const SizeClass& c : p->classes) {
+    for (size_t c0 = 0; c0 < c.items.size(); c0 += hg::kMaxBatch) {
+      const int nb = (int)std::min<size_t>(hg::kMaxBatch, c.items.size() - c0);
+      hg::PassArgs a{};
+      fill_common(p, c, 0, a);
+      a.n_items = nb;
+      a.nmse = nmse_out;
+      a.nmse_stride = n_iter + 1;
+      a.seed = seed;
+      for (int k = 0; k < nb; ++k) {
+        const int item = c.items[c0 + k];
+        a.item_index[k] = item;
+        a.class_slot[k] = (int)(c0 + k);
+        a.target[k] = target_amp[item];
+        a.phase_in[k] = init_phase ? init_phase[item] : nullptr;
+      }
+      const dim3 grow(c.row_blocks(), nb), gcol(c.col_blocks(), nb);
+      // prologue (writes h_0 out when there is no iteration)
+      hg::PassArgs a0 = a;
+      if (n_iter == 0)
+        for (int k = 0; k < nb; ++k) {
+          const int item = c.items[c0 + k];
+          a0.phase_out[k] = phase_out ? phase_out[item] : nullptr;
+          a0.level_out[k] = level_out ? level_out[item] : nullptr;
+        }
+      if ((s = launch(c.rk->init, grow, c.rk->nt, c.rk->smem, a0, st)) != HG_OK) return s;
+      hg::PassArgs ao = a;
+      for (int k = 0; k < nb; ++k) {
+        const int item = c.items[c0 + k];
+        ao.phase_out[k] = phase_out ? phase_out[item] : nullptr;
+        ao.level_out[k] = level_out ? level_out[item] : nullptr;
+      }
+      for (int it = 0; it < n_iter; ++it) {
+        a.iter = it;
+        if ((s = launch(c.ck->gs[1], gcol, c.ck->nt, c.ck->smem, a, st)) != HG_OK) return s;
+        const bool last = it == n_iter - 1;
+        if ((s = launch(c.rk->gs[last], grow, c.rk->nt, c.rk->smem, last ? ao : a, st)) != HG_OK) return s;
+      }
+      a.iter = n_iter;
+      if ((s = launch(c.ck->gs[0], gcol, c.ck->nt, c.ck->smem, a, st)) != HG_OK) return s;
+    }
+  }
+  return HG_OK;
+}
+
+}  // extern "C"

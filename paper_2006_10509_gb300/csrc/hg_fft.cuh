@@ -1,0 +1,399 @@
+// Device-side mixed-radix Stockham FFT engine for the row and column passes.
+//
+// The paper's FFT handler (section "Algorithm Libraries", FFTHandlerCuda) wraps cuFFT; this is a
+// hand-written replacement whose stages can be fused with the pointwise steps of the iteration.
+//
+// A CTA transforms B independent sequences of length N ("rows" of a row tile, or "columns" of a
+// column strip).  Data lives in registers; a stage of radix R with Ns = product of earlier radices
+// runs butterfly j (0 <= j < N/R): it takes inputs n = j + r N/R, multiplies input r by
+// w_{Ns R}^{r (j mod Ns)}, applies an R-point DFT and produces outputs at
+// (j / Ns) Ns R + (j mod Ns) + r Ns (Stockham autosort: natural order out, no bit reversal).
+// Between stages the values are exchanged through shared memory.
+//
+// Two properties are used by the fused kernels:
+//  * the inputs of the first stage and the outputs of the last stage both sit at n = j + r N/R, so a
+//    kernel loads/stores global memory directly from/to the registers of those stages;
+//  * if transform B's first radix equals transform A's last radix, B's first stage takes A's
+//    last-stage outputs without any exchange (plans are run forward, then reversed).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace hg {
+
+// ---------------------------------------------------------------- complex helpers
+
+__device__ __forceinline__ float2 c_add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 c_sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 c_mul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+// a * conj(b)
+__device__ __forceinline__ float2 c_mulc(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y));
+}
+__device__ __forceinline__ float2 c_scale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__device__ __forceinline__ float2 c_conj(float2 a) { return make_float2(a.x, -a.y); }
+
+// multiply by the quarter-turn root of unity of the transform direction: -i (forward), +i (inverse)
+template <bool INV>
+__device__ __forceinline__ float2 c_rot(float2 a) {
+  return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+
+// cos / sin of 2 pi k / 16 for k = 0..15 (exact decimal expansions of cos(pi/8), sin(pi/8), sqrt(2)/2)
+#define HG_C1 0.92387953251128675613f
+#define HG_S1 0.38268343236508977173f
+#define HG_R2 0.70710678118654752440f
+
+// a * w16^K with w16 = exp(-+ 2 pi i / 16)
+template <int K, bool INV>
+__device__ __forceinline__ float2 c_w16(float2 a) {
+  constexpr int k = K & 15;
+  constexpr float cs[16] = {1.f, HG_C1, HG_R2, HG_S1, 0.f, -HG_S1, -HG_R2, -HG_C1,
+                            -1.f, -HG_C1, -HG_R2, -HG_S1, 0.f, HG_S1, HG_R2, HG_C1};
+  constexpr float sn[16] = {0.f, HG_S1, HG_R2, HG_C1, 1.f, HG_C1, HG_R2, HG_S1,
+                            0.f, -HG_S1, -HG_R2, -HG_C1, -1.f, -HG_C1, -HG_R2, -HG_S1};
+  if constexpr (k == 0) {
+    return a;
+  } else if constexpr (k == 4) {
+    return c_rot<INV>(a);
+  } else if constexpr (k == 8) {
+    return make_float2(-a.x, -a.y);
+  } else if constexpr (k == 12) {
+    return c_rot<!INV>(a);
+  } else {
+    // w = cs - i sn (forward) or cs + i sn (inverse)
+    constexpr float c = cs[k];
+    constexpr float s = INV ? sn[k] : -sn[k];
+    return make_float2(fmaf(a.x, c, -a.y * s), fmaf(a.x, s, a.y * c));
+  }
+}
+
+// ---------------------------------------------------------------- small DFTs (in place, natural order)
+
+template <bool INV>
+__device__ __forceinline__ void dft2(float2& a, float2& b) {
+  float2 t = a;
+  a = c_add(t, b);
+  b = c_sub(t, b);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft4(float2& x0, float2& x1, float2& x2, float2& x3) {
+  float2 a = c_add(x0, x2), b = c_sub(x0, x2);
+  float2 c = c_add(x1, x3), d = c_rot<INV>(c_sub(x1, x3));
+  x0 = c_add(a, c);
+  x2 = c_sub(a, c);
+  x1 = c_add(b, d);
+  x3 = c_sub(b, d);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft3(float2* v) {
+  // X1,2 = x0 - (x1+x2)/2 -+ i (sqrt(3)/2)(x1 - x2)   (forward; signs flip for inverse)
+  constexpr float h = 0.86602540378443864676f;
+  float2 s = c_add(v[1], v[2]);
+  float2 d = c_sub(v[1], v[2]);
+  float2 m = make_float2(fmaf(-0.5f, s.x, v[0].x), fmaf(-0.5f, s.y, v[0].y));
+  float2 r = c_rot<INV>(make_float2(h * d.x, h * d.y));  // -+ i (sqrt3/2) d
+  v[0] = c_add(v[0], s);
+  v[1] = c_add(m, r);
+  v[2] = c_sub(m, r);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft5(float2* v) {
+  constexpr float c1 = 0.30901699437494742410f;   // cos(2 pi / 5)
+  constexpr float c2 = -0.80901699437494742410f;  // cos(4 pi / 5)
+  constexpr float s1 = 0.95105651629515357212f;   // sin(2 pi / 5)
+  constexpr float s2 = 0.58778525229247312917f;   // sin(4 pi / 5)
+  float2 a1 = c_add(v[1], v[4]), b1 = c_sub(v[1], v[4]);
+  float2 a2 = c_add(v[2], v[3]), b2 = c_sub(v[2], v[3]);
+  float2 x0 = v[0];
+  float2 p1 = make_float2(x0.x + c1 * a1.x + c2 * a2.x, x0.y + c1 * a1.y + c2 * a2.y);
+  float2 p2 = make_float2(x0.x + c2 * a1.x + c1 * a2.x, x0.y + c2 * a1.y + c1 * a2.y);
+  // q1 = s1 b1 + s2 b2, q2 = s2 b1 - s1 b2 ; X1 = p1 - i q1, X4 = p1 + i q1 (forward)
+  float2 q1 = make_float2(s1 * b1.x + s2 * b2.x, s1 * b1.y + s2 * b2.y);
+  float2 q2 = make_float2(s2 * b1.x - s1 * b2.x, s2 * b1.y - s1 * b2.y);
+  float2 r1 = c_rot<INV>(q1);
+  float2 r2 = c_rot<INV>(q2);
+  v[0] = make_float2(x0.x + a1.x + a2.x, x0.y + a1.y + a2.y);
+  v[1] = c_add(p1, r1);
+  v[4] = c_sub(p1, r1);
+  v[2] = c_add(p2, r2);
+  v[3] = c_sub(p2, r2);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft8(float2* v) {
+  float2 e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+  float2 o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+  dft4<INV>(e0, e1, e2, e3);
+  dft4<INV>(o0, o1, o2, o3);
+  o1 = c_w16<2, INV>(o1);
+  o2 = c_w16<4, INV>(o2);
+  o3 = c_w16<6, INV>(o3);
+  v[0] = c_add(e0, o0);
+  v[4] = c_sub(e0, o0);
+  v[1] = c_add(e1, o1);
+  v[5] = c_sub(e1, o1);
+  v[2] = c_add(e2, o2);
+  v[6] = c_sub(e2, o2);
+  v[3] = c_add(e3, o3);
+  v[7] = c_sub(e3, o3);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft16(float2* v) {
+  // r = 4a + b, q = c + 4d:  X[c + 4d] = sum_b w4^{bd} w16^{bc} sum_a x[4a + b] w4^{ac}
+#pragma unroll
+  for (int b = 0; b < 4; ++b) dft4<INV>(v[b], v[b + 4], v[b + 8], v[b + 12]);
+  // now v[b + 4c] = Y_b[c]; twiddle by w16^{bc}
+  v[5] = c_w16<1, INV>(v[5]);
+  v[9] = c_w16<2, INV>(v[9]);
+  v[13] = c_w16<3, INV>(v[13]);
+  v[6] = c_w16<2, INV>(v[6]);
+  v[10] = c_w16<4, INV>(v[10]);
+  v[14] = c_w16<6, INV>(v[14]);
+  v[7] = c_w16<3, INV>(v[7]);
+  v[11] = c_w16<6, INV>(v[11]);
+  v[15] = c_w16<9, INV>(v[15]);
+#pragma unroll
+  for (int c = 0; c < 4; ++c) dft4<INV>(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
+  // v[4c + d] = X[c + 4d]: transpose the 4x4 block
+  float2 t[16];
+#pragma unroll
+  for (int c = 0; c < 4; ++c)
+#pragma unroll
+    for (int d = 0; d < 4; ++d) t[c + 4 * d] = v[4 * c + d];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = t[i];
+}
+
+template <int R, bool INV>
+__device__ __forceinline__ void dft(float2* v) {
+  if constexpr (R == 2) {
+    dft2<INV>(v[0], v[1]);
+  } else if constexpr (R == 3) {
+    dft3<INV>(v);
+  } else if constexpr (R == 4) {
+    dft4<INV>(v[0], v[1], v[2], v[3]);
+  } else if constexpr (R == 5) {
+    dft5<INV>(v);
+  } else if constexpr (R == 8) {
+    dft8<INV>(v);
+  } else if constexpr (R == 16) {
+    dft16<INV>(v);
+  } else {
+    static_assert(R == 2, "unsupported radix");
+  }
+}
+
+// ---------------------------------------------------------------- radix plans
+
+template <int... Rs>
+struct RList {};
+
+template <class L>
+struct RFirst;
+template <int R, int... Rs>
+struct RFirst<RList<R, Rs...>> {
+  static constexpr int value = R;
+};
+
+template <class L>
+struct RLast;
+template <int R>
+struct RLast<RList<R>> {
+  static constexpr int value = R;
+};
+template <int R, int R2, int... Rs>
+struct RLast<RList<R, R2, Rs...>> {
+  static constexpr int value = RLast<RList<R2, Rs...>>::value;
+};
+
+template <class L, class Acc = RList<>>
+struct RRev;
+template <int... As>
+struct RRev<RList<>, RList<As...>> {
+  using type = RList<As...>;
+};
+template <int R, int... Rs, int... As>
+struct RRev<RList<R, Rs...>, RList<As...>> {
+  using type = typename RRev<RList<Rs...>, RList<R, As...>>::type;
+};
+
+template <class L>
+struct RProd;
+template <>
+struct RProd<RList<>> {
+  static constexpr int value = 1;
+};
+template <int R, int... Rs>
+struct RProd<RList<R, Rs...>> {
+  static constexpr int value = R * RProd<RList<Rs...>>::value;
+};
+
+// Radix plan for each supported length (forward order; the inverse of a fused pair runs reversed).
+template <int N>
+struct PlanFor;
+#define HG_PLAN(N, ...)              \
+  template <>                        \
+  struct PlanFor<N> {                \
+    using type = RList<__VA_ARGS__>; \
+  };
+HG_PLAN(8, 8)
+HG_PLAN(16, 16)
+HG_PLAN(32, 8, 4)
+HG_PLAN(64, 8, 8)
+HG_PLAN(128, 16, 8)
+HG_PLAN(256, 16, 16)
+HG_PLAN(512, 8, 8, 8)
+HG_PLAN(1024, 16, 8, 8)
+HG_PLAN(2048, 16, 16, 8)
+HG_PLAN(4096, 16, 16, 16)
+HG_PLAN(12, 4, 3)
+HG_PLAN(15, 5, 3)
+HG_PLAN(30, 2, 3, 5)
+HG_PLAN(60, 4, 3, 5)
+HG_PLAN(120, 8, 3, 5)
+HG_PLAN(864, 8, 4, 3, 3, 3)
+HG_PLAN(1080, 8, 3, 3, 3, 5)
+HG_PLAN(1536, 16, 8, 4, 3)
+HG_PLAN(1920, 16, 8, 3, 5)
+#undef HG_PLAN
+
+// ---------------------------------------------------------------- tile geometry
+
+// B sequences of length N, NT threads.  COLS: a column strip (element (b, n) of the strip at global
+// row n, column col0 + b; in shared memory at n * B + b).  Otherwise a row tile (element (b, n) at
+// global row row0 + b, column n; in shared memory at b * N + n).
+template <int N_, int B_, int NT_, bool COLS_>
+struct Geo {
+  static constexpr int N = N_;
+  static constexpr int B = B_;
+  static constexpr int NT = NT_;
+  static constexpr bool COLS = COLS_;
+
+  template <int R>
+  __host__ __device__ static constexpr int nbf() {
+    return B * N / R;
+  }
+  template <int R>
+  __host__ __device__ static constexpr int bpt() {
+    return (nbf<R>() + NT - 1) / NT;
+  }
+  template <int R>
+  __host__ __device__ static constexpr bool exact() {
+    return nbf<R>() % NT == 0;
+  }
+
+  __device__ __forceinline__ static int sidx(int b, int n) { return COLS ? n * B + b : b * N + n; }
+
+  // butterfly i of thread t in a radix-R stage -> (sequence b, butterfly j); false when past the end
+  template <int R>
+  __device__ __forceinline__ static bool bf(int t, int i, int& b, int& j) {
+    const int u = t + i * NT;
+    if constexpr (COLS) {
+      b = u % B;
+      j = u / B;
+    } else {
+      j = u % (N / R);
+      b = u / (N / R);
+    }
+    return exact<R>() || u < nbf<R>();
+  }
+};
+
+template <class G, class L>
+struct MaxV;
+template <class G, int R>
+struct MaxV<G, RList<R>> {
+  static constexpr int value = G::template bpt<R>() * R;
+};
+template <class G, int R, int R2, int... Rs>
+struct MaxV<G, RList<R, R2, Rs...>> {
+  static constexpr int a = G::template bpt<R>() * R;
+  static constexpr int b = MaxV<G, RList<R2, Rs...>>::value;
+  static constexpr int value = a > b ? a : b;
+};
+
+// ---------------------------------------------------------------- stage engine
+
+// Visit every value held for a radix-R first/last stage: f(slot, b, n) with n = j + r N / R.
+template <class G, int R, class F>
+__device__ __forceinline__ void for_each_slot(int t, F&& f) {
+#pragma unroll
+  for (int i = 0; i < G::template bpt<R>(); ++i) {
+    int b, j;
+    if (!G::template bf<R>(t, i, b, j)) continue;
+#pragma unroll
+    for (int r = 0; r < R; ++r) f(i * R + r, b, j + r * (G::N / R));
+  }
+}
+
+template <class G, int R, int NS, bool INV, int V>
+__device__ __forceinline__ void stage_compute(float2 (&v)[V], int t, const float2* __restrict__ tw) {
+#pragma unroll
+  for (int i = 0; i < G::template bpt<R>(); ++i) {
+    int b, j;
+    if (!G::template bf<R>(t, i, b, j)) continue;
+    float2* x = &v[i * R];
+    if constexpr (NS > 1) {
+      const int k = j % NS;
+      constexpr int step = G::N / (NS * R);
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        const float2 w = __ldg(&tw[r * k * step]);
+        x[r] = INV ? c_mulc(x[r], w) : c_mul(x[r], w);
+      }
+    }
+    dft<R, INV>(x);
+  }
+}
+
+template <class G, int R, int NS, int V>
+__device__ __forceinline__ void stage_store(const float2 (&v)[V], float2* sm, int t) {
+#pragma unroll
+  for (int i = 0; i < G::template bpt<R>(); ++i) {
+    int b, j;
+    if (!G::template bf<R>(t, i, b, j)) continue;
+    const int base = (j / NS) * NS * R + (j % NS);
+#pragma unroll
+    for (int r = 0; r < R; ++r) sm[G::sidx(b, base + r * NS)] = v[i * R + r];
+  }
+}
+
+template <class G, int R, int V>
+__device__ __forceinline__ void stage_load(float2 (&v)[V], const float2* sm, int t) {
+#pragma unroll
+  for (int i = 0; i < G::template bpt<R>(); ++i) {
+    int b, j;
+    if (!G::template bf<R>(t, i, b, j)) continue;
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[i * R + r] = sm[G::sidx(b, j + r * (G::N / R))];
+  }
+}
+
+// Run all stages of plan L (registers already hold the first stage's inputs); on return the
+// registers hold the last stage's outputs.  Uses sm as the exchange buffer (B*N float2).
+template <class G, bool INV, int NS, class L>
+struct FftRun;
+template <class G, bool INV, int NS, int R, int... Rs>
+struct FftRun<G, INV, NS, RList<R, Rs...>> {
+  template <int V>
+  __device__ __forceinline__ static void run(float2 (&v)[V], float2* sm, int t, const float2* __restrict__ tw) {
+    stage_compute<G, R, NS, INV>(v, t, tw);
+    if constexpr (sizeof...(Rs) > 0) {
+      __syncthreads();  // everyone is done reading sm from the previous exchange
+      stage_store<G, R, NS>(v, sm, t);
+      __syncthreads();
+      stage_load<G, RFirst<RList<Rs...>>::value>(v, sm, t);
+      FftRun<G, INV, NS * R, RList<Rs...>>::run(v, sm, t, tw);
+    }
+  }
+};
+
+}  // namespace hg

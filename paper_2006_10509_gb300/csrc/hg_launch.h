@@ -1,0 +1,43 @@
+// Per-length kernel tables: each supported FFT length is instantiated in its own translation unit
+// (hg_len.cu compiled once per length with -DHG_LEN=N) and looked up at run time by the plan.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace hg {
+
+struct RowKernels {
+  int rows;      // rows per CTA
+  int nt;        // threads per CTA
+  int smem;      // dynamic shared memory bytes
+  const void* init;         // k_row_init
+  const void* gs[2];        // k_row_gs<OUT = false / true>
+  const void* fft[2][2];    // k_row_fft<INV><PRE>
+  void (*set_attrs)();      // raises the dynamic shared-memory limit on the current device
+};
+
+struct ColKernels {
+  int cols;
+  int nt;
+  int smem;
+  const void* gs[2];        // k_col_gs<REPLACE = false / true>
+  const void* fft[2][2];    // k_col_fft<INV><POST>
+  void (*set_attrs)();
+};
+
+// X-macro of every supported FFT length (rows and columns).
+#define HG_FOR_EACH_LENGTH(X) \
+  X(8) X(16) X(32) X(64) X(128) X(256) X(512) X(1024) X(2048) X(4096) \
+  X(12) X(15) X(30) X(60) X(120) X(864) X(1080) X(1536) X(1920)
+
+#define HG_DECLARE_LEN(N)                  \
+  const RowKernels& row_kernels_##N();     \
+  const ColKernels& col_kernels_##N();
+HG_FOR_EACH_LENGTH(HG_DECLARE_LEN)
+#undef HG_DECLARE_LEN
+
+// nullptr when the length is not supported
+const RowKernels* row_kernels(int n);
+const ColKernels* col_kernels(int n);
+
+}  // namespace hg

@@ -1,0 +1,93 @@
+// Instantiates the row- and column-pass kernels for one FFT length, HG_LEN (set by the build).
+#include "hg_kernels.cuh"
+#include "hg_launch.h"
+
+#ifndef HG_LEN
+#error "HG_LEN must be defined"
+#endif
+
+namespace hg {
+
+namespace {
+
+template <class F>
+void allow_smem(F* f, int bytes) {
+  if (bytes > 48 * 1024) cudaFuncSetAttribute((const void*)f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+template <int N>
+RowKernels make_row() {
+  using K = RowCfg<N>;
+  RowKernels r{};
+  r.rows = K::ROWS;
+  r.nt = K::NT;
+  r.smem = K::SMEM;
+  r.init = (const void*)&k_row_init<N>;
+  r.gs[0] = (const void*)&k_row_gs<N, false>;
+  r.gs[1] = (const void*)&k_row_gs<N, true>;
+  r.fft[0][0] = (const void*)&k_row_fft<N, false, false>;
+  r.fft[0][1] = (const void*)&k_row_fft<N, false, true>;
+  r.fft[1][0] = (const void*)&k_row_fft<N, true, false>;
+  r.fft[1][1] = (const void*)&k_row_fft<N, true, true>;
+  return r;
+}
+
+template <int N>
+ColKernels make_col() {
+  using K = ColCfg<N>;
+  ColKernels c{};
+  c.cols = K::C;
+  c.nt = K::NT;
+  c.smem = K::SMEM;
+  c.gs[0] = (const void*)&k_col_gs<N, false>;
+  c.gs[1] = (const void*)&k_col_gs<N, true>;
+  c.fft[0][0] = (const void*)&k_col_fft<N, false, false>;
+  c.fft[0][1] = (const void*)&k_col_fft<N, false, true>;
+  c.fft[1][0] = (const void*)&k_col_fft<N, true, false>;
+  c.fft[1][1] = (const void*)&k_col_fft<N, true, true>;
+  return c;
+}
+
+void set_row_attrs(const RowKernels& r) {
+  allow_smem(&k_row_init<HG_LEN>, r.smem);
+  allow_smem(&k_row_gs<HG_LEN, false>, r.smem);
+  allow_smem(&k_row_gs<HG_LEN, true>, r.smem);
+  allow_smem(&k_row_fft<HG_LEN, false, false>, r.smem);
+  allow_smem(&k_row_fft<HG_LEN, false, true>, r.smem);
+  allow_smem(&k_row_fft<HG_LEN, true, false>, r.smem);
+  allow_smem(&k_row_fft<HG_LEN, true, true>, r.smem);
+}
+
+void set_col_attrs(const ColKernels& c) {
+  allow_smem(&k_col_gs<HG_LEN, false>, c.smem);
+  allow_smem(&k_col_gs<HG_LEN, true>, c.smem);
+  allow_smem(&k_col_fft<HG_LEN, false, false>, c.smem);
+  allow_smem(&k_col_fft<HG_LEN, false, true>, c.smem);
+  allow_smem(&k_col_fft<HG_LEN, true, false>, c.smem);
+  allow_smem(&k_col_fft<HG_LEN, true, true>, c.smem);
+}
+
+}  // namespace
+
+#define HG_CAT2(a, b) a##b
+#define HG_CAT(a, b) HG_CAT2(a, b)
+
+const RowKernels& HG_CAT(row_kernels_, HG_LEN)() {
+  static const RowKernels r = [] {
+    RowKernels x = make_row<HG_LEN>();
+    x.set_attrs = [] { set_row_attrs(make_row<HG_LEN>()); };
+    return x;
+  }();
+  return r;
+}
+
+const ColKernels& HG_CAT(col_kernels_, HG_LEN)() {
+  static const ColKernels c = [] {
+    ColKernels x = make_col<HG_LEN>();
+    x.set_attrs = [] { set_col_attrs(make_col<HG_LEN>()); };
+    return x;
+  }();
+  return c;
+}
+
+}  // namespace hg
