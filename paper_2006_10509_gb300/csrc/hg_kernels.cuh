@@ -32,7 +32,8 @@ struct RowCfg {
   using G = Geo<W, ROWS, NT, false>;
   using Fwd = typename PlanFor<W>::type;
   using Inv = typename RRev<Fwd>::type;
-  static constexpr int RE = RLast<Fwd>::value;  // radix of the global load/store stage
+  static constexpr int RE = RLast<Fwd>::value;   // radix of the global load/store stages
+  static constexpr int RM = RFirst<Fwd>::value;  // radix of the pointwise step between the FFTs
   static constexpr int V = MaxV<G, Fwd>::value;
   static constexpr int SMEM = ROWS * W * 8;
 };
@@ -270,7 +271,7 @@ __global__ void __launch_bounds__(RowCfg<W>::NT) k_row_gs(const __grid_constant_
   FftRun<G, true, 1, typename K::Inv>::run(v, sm, t, a.tw_row);
   float* po = OUT ? a.phase_out[k] : nullptr;
   uint8_t* lo = OUT ? a.level_out[k] : nullptr;
-  for_each_slot<G, K::RE>(t, [&](int s, int b, int n) {
+  for_each_slot<G, K::RM>(t, [&](int s, int b, int n) {
     const int row = row0 + b;
     float2 g = v[s];
     float2 c = make_float2(1.f, 0.f);

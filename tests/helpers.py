@@ -3,7 +3,9 @@
 Comparison rules (GPU float32 vs oracle float64):
 * fields: relative L2 error <= 1e-4 per transform;
 * continuous phase: wrapped angle error <= 1e-4 rad on pixels whose oracle pre-projection field is
-  not tiny (|g| >= 1e-3 rms(g); the phase of a near-zero field is ill-conditioned);
+  not tiny, |g| >= 1e-2 rms(g).  The phase of a small field is ill-conditioned: a float32 FFT
+  round trip leaves an absolute error of a few 1e-7 rms(g) on every pixel, i.e. ~3e-5 rad at
+  |g| = 1e-2 rms but ~3e-4 rad at 1e-3 rms.  At most 0.1 % of pixels may be exempt;
 * quantised phase: level indices equal on >= 99.9 % of pixels, and every mismatch on a non-tiny
   pixel has an oracle pre-quantisation phase within 1e-4 rad of a level boundary;
 * NMSE: within 1 % relative.
@@ -17,7 +19,8 @@ FIELD_TOL = 1e-4
 PHASE_TOL = 1e-4
 NMSE_RTOL = 1e-2
 LEVEL_AGREE = 0.999
-TINY = 1e-3
+TINY = 1e-2
+MAX_EXEMPT = 1e-3
 
 
 def cuda_device():
@@ -47,6 +50,7 @@ def not_tiny(g) -> np.ndarray:
 
 def check_continuous_phase(phase_gpu, g_oracle, h_oracle):
     ok = not_tiny(g_oracle)
+    assert np.mean(~ok) <= MAX_EXEMPT, f"{np.mean(~ok):.2e} of pixels exempt"
     err = np.abs(wrap(np.asarray(phase_gpu, dtype=np.float64) - np.angle(h_oracle)))
     worst = float(err[ok].max()) if np.any(ok) else 0.0
     assert worst <= PHASE_TOL, f"max wrapped phase error {worst:.3e} rad"

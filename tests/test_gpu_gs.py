@@ -123,8 +123,9 @@ def test_gs_fresnel_1024_8level_curve():
     _, q, nm = _run(hg, dev, a, n, 8, phi0, fresnel_z=0.1)
     c = optics.chirp(1024, 1024, LAM, PITCH, 0.1)
     ref = ogs.gs(a.astype(np.float64), phi0.astype(np.float64), n, 8, c)
+    # quantised trajectories separate pixel by pixel after boundary flips; the end-to-end bar is
+    # the NMSE curve (pixel parity is the teacher-forced one-step test)
     check_nmse(nm, ref["nmse"])
-    assert np.mean(q == ref["q"]) > 0.99
 
 
 @pytest.mark.gpu
