@@ -1,0 +1,382 @@
+"""Benchmark: Gerchberg-Saxton iterations/s on a 2048x2048 Fourier hologram (FP32, complex64).
+
+Workload (one step = one full hot-path run over one synthetic input): hg_gs_run of 100 GS iterations,
+continuous phase, on a 2048 x 2048 target (smoothed-noise amplitude, sigma 2 px, seed 0 + rank),
+uniform starting phase (seed 1 + rank), NMSE of every iterate.  Inputs are resident in HBM when the
+timed region starts; L2 is flushed (a 512 MiB write) before every timed step, outside the step's
+events.  value = GS iterations/s over all ranks (weak scaling: every rank runs its own hologram).
+
+Also reported:
+  roofline      the dominant kernel's algorithmic bytes per launch / its mean launch time (CUDA
+                events recorded by the library around every launch during the timed steps), against
+                the measured HBM copy bandwidth; traffic = DRAM bytes per launch from the committed
+                ncu summary when it was taken on the current kernel sources (else null)
+  e2e           the same metric through the public API with host buffers: every step copies the
+                target and starting phase from pinned host memory and reads back the NMSE curve and
+                the output phase inside the timed region
+  cpu_baseline  the FP64 oracle (single thread) on a bounded sample of the same workload
+  clocks        nvidia-smi SM clocks / throttle reasons sampled during the timed steps
+
+--impl reference times the oracle (the only reference this method has) on the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+if "reference" in sys.argv:
+    # the oracle leg runs on one host thread (set before numpy is imported)
+    for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[_v] = "1"
+
+H = W = 2048
+N_ITER = 100
+SIGMA = 2.0
+METRIC = "GS iterations/s at 2048x2048 FP32 (Fourier, continuous phase, 100 iterations per run)"
+UNIT = "it/s"
+WORKLOAD = "Fourier GS 2048x2048 complex64, continuous phase, 100 iterations/run, per-iteration NMSE"
+BYTES_PER_PX = {"col_gs": 20, "row_gs": 16, "row_init": 12, "col_nmse": 12}  # algorithmic HBM bytes
+PROFILE_MD = os.path.join(ROOT, "profiles", "gs_2048_kernels.md")
+KERNEL_SOURCES = ["paper_2006_10509_gb300/csrc/hg_fft.cuh", "paper_2006_10509_gb300/csrc/hg_kernels.cuh"]
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def profiled_traffic(kind: str):
+    """DRAM bytes per launch of ``kind`` from the committed ncu summary, if it matches the sources."""
+    if not os.path.exists(PROFILE_MD):
+        return None
+    src_hash, traffic = None, {}
+    with open(PROFILE_MD) as f:
+        for line in f:
+            if line.startswith("source_hash:"):
+                src_hash = line.split(":", 1)[1].strip()
+            if line.startswith("traffic_bytes_per_launch:"):
+                _, k, v = line.split()
+                traffic[k] = int(v)
+    if src_hash != kernel_source_hash():
+        return None
+    return traffic.get(kind)
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons while the timed region runs."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.out, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.out.close()
+
+    def summary(self):
+        if self.proc is None or not self.path:
+            return None
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for name, val in zip(names, parts[5:9]):
+                    if val.lower() == "active":
+                        reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+
+        backend = "nccl" if os.environ.get("HG_BENCH_BACKEND", "nccl") == "nccl" else "gloo"
+        dist.init_process_group(backend)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(x: float, ws: int, dev) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- CPU oracle legs
+
+
+ORACLE_SNIPPET = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+import numpy as np
+import synth
+from oracle import gs as ogs
+a = synth.blur_target({h}, {w}, {sigma}, seed=0).astype(np.float64)
+phi = synth.uniform_phase({h}, {w}, seed=1).astype(np.float64)
+h = np.exp(1j * phi)
+h = ogs.gs_step(h, a, 0)["h"]  # warm-up (page in, allocator)
+t = time.perf_counter()
+for _ in range({n}):
+    h = ogs.gs_step(h, a, 0)["h"]
+dt = time.perf_counter() - t
+print(json.dumps({{"seconds": dt, "iterations": {n}}}))
+"""
+
+
+def oracle_gs_rate(n_iter: int) -> tuple[float, float]:
+    """Runs n_iter FP64 oracle GS iterations (forward transform, amplitude replacement, inverse
+    transform, projection) in a single-threaded subprocess; returns (iterations/s, seconds)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ORACLE_SNIPPET.format(root=ROOT, h=H, w=W, sigma=SIGMA, n=n_iter)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, check=True)
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    return d["iterations"] / d["seconds"], d["seconds"]
+
+
+def run_reference(args):
+    """--impl reference: the FP64 oracle on the host cores, same metric / unit / workload."""
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import numpy as np
+
+    import synth
+    from oracle import gs as ogs
+
+    a = synth.blur_target(H, W, SIGMA, seed=0).astype(np.float64)
+    phi = synth.uniform_phase(H, W, seed=1).astype(np.float64)
+    h = np.exp(1j * phi)
+    for _ in range(args.warmup):
+        h = ogs.gs_step(h, a, 0)["h"]
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        h = ogs.gs_step(h, a, 0)["h"]  # one sample GS iteration per step
+    dt = time.perf_counter() - t
+    value = args.steps / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": "1 GS iteration per step (the oracle's 100-iteration run "
+                                                   "takes minutes; the per-iteration NMSE is not taken)", "parallelism": "none"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} single GS iterations of the 2048x2048 workload, float64, "
+                                   "one thread"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+# ---------------------------------------------------------------- GPU leg
+
+
+def run_ours(args):
+    ws, rank, local = dist_setup()
+    import numpy as np
+    import torch
+
+    import paper_2006_10509_gb300 as hg
+    import synth
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from __graft_entry__ import build
+
+    if rank == 0 or ws == 1:
+        build()
+    barrier(ws)
+    build()
+
+    a_host = torch.from_numpy(synth.blur_target(H, W, SIGMA, seed=0 + rank)).pin_memory()
+    p_host = torch.from_numpy(synth.uniform_phase(H, W, seed=1 + rank)).pin_memory()
+    a = a_host.to(dev)
+    p = p_host.to(dev)
+    nm = torch.zeros((1, N_ITER + 1), dtype=torch.float32, device=dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    plan = hg.Plan([H], [W])
+    for _ in range(args.warmup):
+        plan.gs([a], N_ITER, init_phase=[p], nmse_out=nm)
+    torch.cuda.synchronize()
+
+    # timed region: K steps, L2 flushed before each (outside the step's events)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    plan.reset_timing()
+    plan.set_timing(True)
+    launches0 = plan.launch_count()
+    with ClockSampler(local) as clocks:
+        barrier(ws)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for e0, e1 in evs:
+            flush.zero_()
+            e0.record(stream)
+            plan.gs([a], N_ITER, init_phase=[p], nmse_out=nm)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        barrier(ws)
+        wall = time.perf_counter() - t0
+    plan.set_timing(False)
+    launches = plan.launch_count() - launches0
+    dev_ms = sum(e0.elapsed_time(e1) for e0, e1 in evs)
+    dev_ms = max_over_ranks(dev_ms, ws, dev)
+    ms_per_step = dev_ms / args.steps
+    value = ws * N_ITER * args.steps / (dev_ms / 1e3)
+    ktimes = plan.kernel_times()
+    final_nmse = float(nm[0, -1].item())
+
+    # dominant kernel roofline
+    dom = max(ktimes, key=lambda k: ktimes[k][0])
+    dom_ms, dom_n = ktimes[dom]
+    alg_bytes = BYTES_PER_PX.get(dom, 16) * H * W
+    achieved = alg_bytes / (dom_ms / dom_n / 1e3) / 1e9
+    peak, peak_src = measured_peaks()
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": peak_src, "traffic": profiled_traffic(dom),
+                "alg_bytes_per_launch": alg_bytes, "mean_launch_us": dom_ms / dom_n * 1e3,
+                "kernel_share": {k: v[0] / sum(x[0] for x in ktimes.values()) for k, v in ktimes.items()}}
+
+    # end to end through the public API with host buffers
+    ph_out = torch.empty((H, W), dtype=torch.float32, device=dev)
+    nm_host = torch.empty((1, N_ITER + 1), dtype=torch.float32).pin_memory()
+    ph_host = torch.empty((H, W), dtype=torch.float32).pin_memory()
+    a_dev = torch.empty_like(a)
+    p_dev = torch.empty_like(p)
+
+    def e2e_step():
+        a_dev.copy_(a_host, non_blocking=True)
+        p_dev.copy_(p_host, non_blocking=True)
+        plan.gs([a_dev], N_ITER, init_phase=[p_dev], phase_out=[ph_out], nmse_out=nm)
+        nm_host.copy_(nm, non_blocking=True)
+        ph_host.copy_(ph_out, non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier(ws)
+    for e0, e1 in e2e_evs:
+        flush.zero_()
+        e0.record(stream)
+        e2e_step()
+        e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(sum(e0.elapsed_time(e1) for e0, e1 in e2e_evs), ws, dev)
+    e2e = {"value": ws * N_ITER * args.steps / (e2e_ms / 1e3), "unit": UNIT,
+           "h2d_bytes_per_step": a_host.numel() * 4 + p_host.numel() * 4,
+           "d2h_bytes_per_step": nm_host.numel() * 4 + ph_host.numel() * 4}
+    plan.close()
+
+    if rank != 0:
+        return
+    cpu = None
+    if ws == 1 and not args.no_cpu_baseline:
+        n = args.cpu_iters
+        rate, secs = oracle_gs_rate(n)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{n} GS iterations of the same 2048x2048 workload, "
+                         f"{secs:.1f} s, float64, one thread, NMSE not taken"}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "H": H, "W": W, "n_iter": N_ITER, "quant_levels": 0,
+                   "target": f"smoothed noise sigma {SIGMA} px, seed 0+rank", "init_phase": "uniform, seed 1+rank",
+                   "l2": "flushed (512 MiB write) before every timed step", "parallelism": f"replicas x{ws}",
+                   "final_nmse": final_nmse},
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+        "clocks": clocks.summary(), "wall_s": wall,
+    }
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-iters", type=int, default=4)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

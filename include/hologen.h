@@ -126,6 +126,20 @@ HG_API hg_status hg_gs_run(hg_plan* plan, const float* const* target_amp, const 
                     uint64_t seed, int32_t n_iter, float* const* phase_out, uint8_t* const* level_out,
                     float* nmse_out, void* stream);
 
+/*
+ * Kernel timing (tracing aid; no counterpart in the paper).  While enabled, every kernel the plan
+ * launches is bracketed by two CUDA events on its stream and its device time is added to the
+ * total of its kind.  hg_plan_kernel_time synchronises the plan's device, folds the pending events
+ * in and returns (total milliseconds, launches) for one kind; hg_kernel_kind_name names the kinds
+ * (NULL past the last).  hg_plan_launch_count counts every kernel launched by the plan since
+ * creation, timed or not.
+ */
+HG_API hg_status hg_plan_set_timing(hg_plan* plan, int32_t enabled);
+HG_API hg_status hg_plan_kernel_time(hg_plan* plan, int32_t kind, double* total_ms, int64_t* launches);
+HG_API hg_status hg_plan_reset_timing(hg_plan* plan);
+HG_API const char* hg_kernel_kind_name(int32_t kind);
+HG_API int64_t hg_plan_launch_count(const hg_plan* plan);
+
 /* Human-readable name of a status code (static string). */
 HG_API const char* hg_status_string(hg_status status);
 

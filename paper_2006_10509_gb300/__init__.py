@@ -21,6 +21,8 @@ __all__ = [
     "HG_ERR_TIMEOUT", "HG_ERR_INTERNAL", "HG_FOURIER", "HG_FRESNEL",
     "HologenError", "lib_path", "load", "hg_plan_create", "hg_plan_destroy", "hg_plan_sync",
     "hg_propagate", "hg_gs_run", "hg_status_string", "hg_last_error", "hg_supported_length", "Plan",
+    "hg_plan_set_timing", "hg_plan_reset_timing", "hg_plan_kernel_time", "hg_kernel_kind_name",
+    "hg_plan_launch_count",
 ]
 
 HG_OK, HG_ERR_INVALID_ARG, HG_ERR_UNSUPPORTED_SIZE, HG_ERR_OUT_OF_MEMORY = 0, 1, 2, 3
@@ -65,6 +67,12 @@ _SIGNATURES = {
     "hg_plan_sync": (ctypes.c_int, [_VP]),
     "hg_propagate": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32, _PP, _PP, _VP]),
     "hg_gs_run": (ctypes.c_int, [_VP, _PP, _PP, ctypes.c_uint64, ctypes.c_int32, _PP, _PP, _VP, _VP]),
+    "hg_plan_set_timing": (ctypes.c_int, [_VP, ctypes.c_int32]),
+    "hg_plan_reset_timing": (ctypes.c_int, [_VP]),
+    "hg_plan_kernel_time": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
+                                           ctypes.POINTER(ctypes.c_int64)]),
+    "hg_kernel_kind_name": (ctypes.c_char_p, [ctypes.c_int32]),
+    "hg_plan_launch_count": (ctypes.c_int64, [_VP]),
     "hg_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "hg_last_error": (ctypes.c_char_p, []),
     "hg_supported_length": (ctypes.c_int32, [ctypes.c_int32]),
@@ -176,6 +184,30 @@ def hg_gs_run(plan: int, target_amp, init_phase=None, seed: int = 0, n_iter: int
                             None if nmse_out is None else _data_ptr(nmse_out), _stream(stream)), "hg_gs_run")
 
 
+def hg_plan_set_timing(plan: int, enabled: bool):
+    _check(load().hg_plan_set_timing(plan, int(bool(enabled))), "hg_plan_set_timing")
+
+
+def hg_plan_reset_timing(plan: int):
+    _check(load().hg_plan_reset_timing(plan), "hg_plan_reset_timing")
+
+
+def hg_plan_kernel_time(plan: int, kind: int) -> tuple[float, int]:
+    ms = ctypes.c_double()
+    n = ctypes.c_int64()
+    _check(load().hg_plan_kernel_time(plan, kind, ctypes.byref(ms), ctypes.byref(n)), "hg_plan_kernel_time")
+    return ms.value, n.value
+
+
+def hg_kernel_kind_name(kind: int) -> str | None:
+    r = load().hg_kernel_kind_name(kind)
+    return None if r is None else r.decode()
+
+
+def hg_plan_launch_count(plan: int) -> int:
+    return int(load().hg_plan_launch_count(plan))
+
+
 class Plan:
     """Owning wrapper around a plan handle (destroyed on close / exit / garbage collection)."""
 
@@ -214,3 +246,23 @@ class Plan:
 
     def sync(self):
         hg_plan_sync(self.handle)
+
+    def set_timing(self, enabled=True):
+        hg_plan_set_timing(self.handle, enabled)
+
+    def reset_timing(self):
+        hg_plan_reset_timing(self.handle)
+
+    def kernel_times(self) -> dict[str, tuple[float, int]]:
+        """{kind name: (total ms, launches)} for every kind launched while timing was on."""
+        out = {}
+        k = 0
+        while (name := hg_kernel_kind_name(k)) is not None:
+            ms, n = hg_plan_kernel_time(self.handle, k)
+            if n:
+                out[name] = (ms, n)
+            k += 1
+        return out
+
+    def launch_count(self) -> int:
+        return hg_plan_launch_count(self.handle)

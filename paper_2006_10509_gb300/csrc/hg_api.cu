@@ -83,6 +83,10 @@ range_fn_t range_fn() {
 }
 
 constexpr int kMaxItems = 256;
+
+// Kernel kinds for the timing facility.
+enum Kind { K_ROW_INIT = 0, K_ROW_GS, K_COL_GS, K_COL_NMSE, K_ROW_FFT, K_COL_FFT, K_NUM_KINDS };
+const char* const kKindNames[K_NUM_KINDS] = {"row_init", "row_gs", "col_gs", "col_nmse", "row_fft", "col_fft"};
 constexpr int kMaxLevels = 256;
 
 struct SizeClass {
@@ -131,9 +135,53 @@ struct hg_plan {
   float2* lev = nullptr;
   float* lev_phase = nullptr;
   std::vector<void*> allocs;
+  // timing facility
+  bool timing = false;
+  int64_t launches = 0;
+  struct Pending {
+    cudaEvent_t a, b;
+    int kind;
+  };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> event_pool;
+  double kind_ms[K_NUM_KINDS] = {};
+  int64_t kind_count[K_NUM_KINDS] = {};
 
   ~hg_plan() {
     for (void* p : allocs) cudaFree(p);
+    for (auto& q : pending) {
+      cudaEventDestroy(q.a);
+      cudaEventDestroy(q.b);
+    }
+    for (cudaEvent_t e : event_pool) cudaEventDestroy(e);
+  }
+  cudaEvent_t get_event() {
+    if (!event_pool.empty()) {
+      cudaEvent_t e = event_pool.back();
+      event_pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    return e;
+  }
+  // folds completed timing events into the per-kind totals (device must be idle)
+  void fold() {
+    for (auto& q : pending) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, q.a, q.b) == cudaSuccess) {
+        kind_ms[q.kind] += ms;
+        kind_count[q.kind] += 1;
+      } else {
+        cudaGetLastError();
+      }
+      event_pool.push_back(q.a);
+      event_pool.push_back(q.b);
+    }
+    pending.clear();
   }
   template <class T>
   hg_status alloc(T** p, size_t count, const char* what) {
@@ -174,10 +222,25 @@ hg_status check_ptr(const hg_plan* p, const void* ptr, size_t bytes, size_t alig
   return HG_OK;
 }
 
-hg_status launch(const void* fn, dim3 grid, int nt, int smem, const hg::PassArgs& a, cudaStream_t s) {
+hg_status launch(hg_plan* p, int kind, const void* fn, dim3 grid, int nt, int smem, const hg::PassArgs& a,
+                 cudaStream_t s) {
   void* args[] = {(void*)&a};
+  cudaEvent_t ea = nullptr, eb = nullptr;
+  if (p->timing) {
+    ea = p->get_event();
+    eb = p->get_event();
+    if (ea && eb) cudaEventRecord(ea, s);
+  }
   cudaError_t e = cudaLaunchKernel(fn, grid, dim3(nt), args, (size_t)smem, s);
   if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+  p->launches++;
+  if (ea && eb) {
+    cudaEventRecord(eb, s);
+    p->pending.push_back({ea, eb, kind});
+  } else {
+    if (ea) p->event_pool.push_back(ea);
+    if (eb) p->event_pool.push_back(eb);
+  }
   return HG_OK;
 }
 
@@ -247,6 +310,41 @@ const char* hg_status_string(hg_status s) {
 }
 
 const char* hg_last_error(void) { return g_err.c_str(); }
+
+hg_status hg_plan_set_timing(hg_plan* p, int32_t enabled) {
+  if (!p) return fail(HG_ERR_INVALID_ARG, "plan is NULL");
+  p->timing = enabled != 0;
+  return HG_OK;
+}
+
+hg_status hg_plan_reset_timing(hg_plan* p) {
+  if (!p) return fail(HG_ERR_INVALID_ARG, "plan is NULL");
+  DeviceGuard g(p->device);
+  cudaDeviceSynchronize();
+  p->fold();
+  for (int k = 0; k < K_NUM_KINDS; ++k) {
+    p->kind_ms[k] = 0.0;
+    p->kind_count[k] = 0;
+  }
+  return HG_OK;
+}
+
+hg_status hg_plan_kernel_time(hg_plan* p, int32_t kind, double* total_ms, int64_t* launches) {
+  if (!p) return fail(HG_ERR_INVALID_ARG, "plan is NULL");
+  if (kind < 0 || kind >= K_NUM_KINDS) return fail(HG_ERR_INVALID_ARG, "kind %d out of range", kind);
+  if (!total_ms || !launches) return fail(HG_ERR_INVALID_ARG, "output is NULL");
+  DeviceGuard g(p->device);
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(e, "device error");
+  p->fold();
+  *total_ms = p->kind_ms[kind];
+  *launches = p->kind_count[kind];
+  return HG_OK;
+}
+
+const char* hg_kernel_kind_name(int32_t kind) { return kind >= 0 && kind < K_NUM_KINDS ? kKindNames[kind] : nullptr; }
+
+int64_t hg_plan_launch_count(const hg_plan* p) { return p ? p->launches : 0; }
 
 int32_t hg_supported_length(int32_t n) { return hg::row_kernels(n) != nullptr && hg::col_kernels(n) != nullptr; }
 
@@ -417,9 +515,9 @@ hg_status hg_propagate(hg_plan* p, int32_t plane, int32_t direction, const void*
         a.in[k] = (const float2*)in[item];
         a.out[k] = (float2*)out[item];
       }
-      if ((s = launch(c.rk->fft[inv][fres && !inv], dim3(c.row_blocks(), nb), c.rk->nt, c.rk->smem, a, st)) != HG_OK)
+      if ((s = launch(p, K_ROW_FFT, c.rk->fft[inv][fres && !inv], dim3(c.row_blocks(), nb), c.rk->nt, c.rk->smem, a, st)) != HG_OK)
         return s;
-      if ((s = launch(c.ck->fft[inv][fres && inv], dim3(c.col_blocks(), nb), c.ck->nt, c.ck->smem, a, st)) != HG_OK)
+      if ((s = launch(p, K_COL_FFT, c.ck->fft[inv][fres && inv], dim3(c.col_blocks(), nb), c.ck->nt, c.ck->smem, a, st)) != HG_OK)
         return s;
     }
   }
@@ -477,7 +575,7 @@ hg_status hg_gs_run(hg_plan* p, const float* const* target_amp, const float* con
           a0.phase_out[k] = phase_out ? phase_out[item] : nullptr;
           a0.level_out[k] = level_out ? level_out[item] : nullptr;
         }
-      if ((s = launch(c.rk->init, grow, c.rk->nt, c.rk->smem, a0, st)) != HG_OK) return s;
+      if ((s = launch(p, K_ROW_INIT, c.rk->init, grow, c.rk->nt, c.rk->smem, a0, st)) != HG_OK) return s;
       hg::PassArgs ao = a;
       for (int k = 0; k < nb; ++k) {
         const int item = c.items[c0 + k];
@@ -486,12 +584,12 @@ hg_status hg_gs_run(hg_plan* p, const float* const* target_amp, const float* con
       }
       for (int it = 0; it < n_iter; ++it) {
         a.iter = it;
-        if ((s = launch(c.ck->gs[1], gcol, c.ck->nt, c.ck->smem, a, st)) != HG_OK) return s;
+        if ((s = launch(p, K_COL_GS, c.ck->gs[1], gcol, c.ck->nt, c.ck->smem, a, st)) != HG_OK) return s;
         const bool last = it == n_iter - 1;
-        if ((s = launch(c.rk->gs[last], grow, c.rk->nt, c.rk->smem, last ? ao : a, st)) != HG_OK) return s;
+        if ((s = launch(p, K_ROW_GS, c.rk->gs[last], grow, c.rk->nt, c.rk->smem, last ? ao : a, st)) != HG_OK) return s;
       }
       a.iter = n_iter;
-      if ((s = launch(c.ck->gs[0], gcol, c.ck->nt, c.ck->smem, a, st)) != HG_OK) return s;
+      if ((s = launch(p, K_COL_NMSE, c.ck->gs[0], gcol, c.ck->nt, c.ck->smem, a, st)) != HG_OK) return s;
     }
   }
   return HG_OK;
