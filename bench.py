@@ -8,7 +8,8 @@ events.  value = GS iterations/s over all ranks (weak scaling: every rank runs i
 
 Also reported:
   roofline      the dominant kernel's algorithmic bytes per launch / its mean launch time (CUDA
-                events recorded by the library around every launch during the timed steps), against
+                events recorded by the library around every launch of the last tenth of the timed
+                steps), against
                 the measured HBM copy bandwidth; traffic = DRAM bytes per launch from the committed
                 ncu summary when it was taken on the current kernel sources (else null)
   e2e           the same metric through the public API with host buffers: every step copies the
@@ -272,14 +273,18 @@ def run_ours(args):
 
     # timed region: K steps, L2 flushed before each (outside the step's events)
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    # per-launch kernel events (for the roofline) on the last tenth of the timed steps only: two extra
+    # event records per launch slow a step down by several percent
+    n_kt = max(1, args.steps // 10)
     plan.reset_timing()
-    plan.set_timing(True)
     launches0 = plan.launch_count()
     with ClockSampler(local) as clocks:
         barrier(ws)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for e0, e1 in evs:
+        for i, (e0, e1) in enumerate(evs):
+            if i == args.steps - n_kt:
+                plan.set_timing(True)
             flush.zero_()
             e0.record(stream)
             plan.gs([a], N_ITER, init_phase=[p], nmse_out=nm)
