@@ -127,6 +127,31 @@ HG_API hg_status hg_gs_run(hg_plan* plan, const float* const* target_amp, const 
                     float* nmse_out, void* stream);
 
 /*
+ * Gerchberg-Saxton for ONE Fourier hologram without allocating device memory.  The paper has no
+ * counterpart: this exists for callers that cannot call cudaMalloc -- code running inside a memory
+ * arena it does not own, plug-ins whose host forbids allocation after start-up, real-time loops in
+ * which an allocation (it may synchronise the device) would break the latency budget -- and so
+ * cannot create a plan.
+ *
+ * Same algorithm, kernels and argument meanings as hg_gs_run with a one-item, one-plane Fourier plan
+ * (quant_levels as in hg_plan_desc; target_amp, init_phase, phase_out, level_out are single device
+ * pointers; nmse_out is [n_iter + 1]).  Its scratch (field, reduction partials and counter, twiddle
+ * and level tables) is a static device array of 8 MiB + 91 KiB that every device which loads this
+ * library keeps until the process exits.
+ *  - Limits: height * width <= 1048576 pixels, each a supported FFT length; larger sizes return
+ *    HG_ERR_UNSUPPORTED_SIZE before anything is launched.
+ *  - The first call on a device looks up the array's device address (cudaGetSymbolAddress), so make
+ *    that first call before any stream capture.
+ *  - Calls no cudaMalloc / cudaFree or allocating routine.  Every call shares the one array and
+ *    leaves its contents behind; the call re-initialises what must start fresh (block counter,
+ *    tables) on its stream.  Calls that overlap on the GPU (different streams, other host threads)
+ *    race on the array and give wrong results: serialise them.
+ */
+HG_API hg_status hg_gs_run_noalloc(int32_t height, int32_t width, int32_t quant_levels, const float* target_amp,
+                                   const float* init_phase, uint64_t seed, int32_t n_iter, float* phase_out,
+                                   uint8_t* level_out, float* nmse_out, void* stream);
+
+/*
  * Kernel timing (tracing aid; no counterpart in the paper).  While enabled, every kernel the plan
  * launches is bracketed by two CUDA events on its stream and its device time is added to the
  * total of its kind.  hg_plan_kernel_time synchronises the plan's device, folds the pending events

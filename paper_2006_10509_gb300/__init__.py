@@ -22,7 +22,7 @@ __all__ = [
     "HologenError", "lib_path", "load", "hg_plan_create", "hg_plan_destroy", "hg_plan_sync",
     "hg_propagate", "hg_gs_run", "hg_status_string", "hg_last_error", "hg_supported_length", "Plan",
     "hg_plan_set_timing", "hg_plan_reset_timing", "hg_plan_kernel_time", "hg_kernel_kind_name",
-    "hg_plan_launch_count",
+    "hg_plan_launch_count", "hg_gs_run_noalloc",
 ]
 
 HG_OK, HG_ERR_INVALID_ARG, HG_ERR_UNSUPPORTED_SIZE, HG_ERR_OUT_OF_MEMORY = 0, 1, 2, 3
@@ -67,6 +67,8 @@ _SIGNATURES = {
     "hg_plan_sync": (ctypes.c_int, [_VP]),
     "hg_propagate": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32, _PP, _PP, _VP]),
     "hg_gs_run": (ctypes.c_int, [_VP, _PP, _PP, ctypes.c_uint64, ctypes.c_int32, _PP, _PP, _VP, _VP]),
+    "hg_gs_run_noalloc": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _VP, _VP, ctypes.c_uint64,
+                                         ctypes.c_int32, _VP, _VP, _VP, _VP]),
     "hg_plan_set_timing": (ctypes.c_int, [_VP, ctypes.c_int32]),
     "hg_plan_reset_timing": (ctypes.c_int, [_VP]),
     "hg_plan_kernel_time": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
@@ -182,6 +184,21 @@ def hg_gs_run(plan: int, target_amp, init_phase=None, seed: int = 0, n_iter: int
     _check(load().hg_gs_run(plan, _ptr_array(target_amp), _ptr_array(init_phase), seed, n_iter,
                             _ptr_array(phase_out), _ptr_array(level_out),
                             None if nmse_out is None else _data_ptr(nmse_out), _stream(stream)), "hg_gs_run")
+
+
+def hg_gs_run_noalloc(height: int, width: int, quant_levels: int, target_amp, init_phase=None, seed: int = 0,
+                      n_iter: int = 1, phase_out=None, level_out=None, nmse_out=None, stream=None):
+    """GS for one Fourier hologram with no device allocation (static scratch; see hologen.h).
+
+    For callers that cannot allocate device memory and so cannot hold a plan.  Tensors are single
+    device tensors (not lists); calls that overlap on the GPU share the scratch and race.
+    """
+
+    def p(t):
+        return None if t is None else _data_ptr(t)
+
+    _check(load().hg_gs_run_noalloc(height, width, quant_levels, p(target_amp), p(init_phase), seed, n_iter,
+                                    p(phase_out), p(level_out), p(nmse_out), _stream(stream)), "hg_gs_run_noalloc")
 
 
 def hg_plan_set_timing(plan: int, enabled: bool):

@@ -47,8 +47,12 @@ const ColKernels* col_kernels(int n) {
 }  // namespace hg
 
 namespace {
-
 thread_local std::string g_err;
+}  // namespace
+
+void hg::set_last_error(const char* msg) { g_err = msg ? msg : ""; }
+
+namespace {
 
 hg_status fail(hg_status s, const char* fmt, ...) {
   char buf[512];

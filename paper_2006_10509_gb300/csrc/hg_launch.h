@@ -40,4 +40,7 @@ HG_FOR_EACH_LENGTH(HG_DECLARE_LEN)
 const RowKernels* row_kernels(int n);
 const ColKernels* col_kernels(int n);
 
+// Sets the detail string returned by hg_last_error() on this host thread.
+void set_last_error(const char* msg);
+
 }  // namespace hg
