@@ -127,6 +127,24 @@ HG_API hg_status hg_gs_run(hg_plan* plan, const float* const* target_amp, const 
                     float* nmse_out, void* stream);
 
 /*
+ * One-Step Phase-Retrieval (Cable, Buckley et al.; section "Algorithm Libraries",
+ * HoloGenAlgOSPRCuda): for every item (target t) and subframe s = 0..n_subframes-1
+ *   E = A exp(2 pi i u),  u = (x >> 8) 2^-24,  x = word 0 of Philox4x32-10 with counter
+ *       (pixel, s, 0, 0) and key (seed_lo, seed_hi ^ t)
+ *   h_s = binary(conj(c) F^-1(E))           (+ n_iter binary GS iterations against A)
+ *   I_acc += |F(h_s c)|^2,   nmse_out[t][s] = NMSE(I_acc, A^2)
+ * Binary projection as in hg_plan_desc (N = 2, h = +1 / -1), whatever the plan's quant_levels.
+ *  target_amp[t]  float32 [H][W] amplitude (FFT order).  A real hologram has a point-symmetric
+ *                 replay, so only the symmetric part of a target is reachable.
+ *  bits_out       NULL, or per item NULL / uint32 [n_subframes][H][ceil(W/32)]: bit (w*32 + i) of
+ *                 row word w is pixel w*32 + i, 1 = phase pi.
+ *  nmse_out       NULL or device float32 [n_items][n_subframes].
+ * The plan allocates an intensity buffer (4 bytes per pixel) on the first call.
+ */
+HG_API hg_status hg_ospr_run(hg_plan* plan, const float* const* target_amp, int32_t n_subframes, int32_t n_iter,
+                             uint64_t seed, uint32_t* const* bits_out, float* nmse_out, void* stream);
+
+/*
  * Gerchberg-Saxton for ONE Fourier hologram without allocating device memory.  The paper has no
  * counterpart: this exists for callers that cannot call cudaMalloc -- code running inside a memory
  * arena it does not own, plug-ins whose host forbids allocation after start-up, real-time loops in

@@ -22,7 +22,7 @@ __all__ = [
     "HologenError", "lib_path", "load", "hg_plan_create", "hg_plan_destroy", "hg_plan_sync",
     "hg_propagate", "hg_gs_run", "hg_status_string", "hg_last_error", "hg_supported_length", "Plan",
     "hg_plan_set_timing", "hg_plan_reset_timing", "hg_plan_kernel_time", "hg_kernel_kind_name",
-    "hg_plan_launch_count", "hg_gs_run_noalloc",
+    "hg_plan_launch_count", "hg_gs_run_noalloc", "hg_ospr_run",
 ]
 
 HG_OK, HG_ERR_INVALID_ARG, HG_ERR_UNSUPPORTED_SIZE, HG_ERR_OUT_OF_MEMORY = 0, 1, 2, 3
@@ -67,6 +67,7 @@ _SIGNATURES = {
     "hg_plan_sync": (ctypes.c_int, [_VP]),
     "hg_propagate": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32, _PP, _PP, _VP]),
     "hg_gs_run": (ctypes.c_int, [_VP, _PP, _PP, ctypes.c_uint64, ctypes.c_int32, _PP, _PP, _VP, _VP]),
+    "hg_ospr_run": (ctypes.c_int, [_VP, _PP, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64, _PP, _VP, _VP]),
     "hg_gs_run_noalloc": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _VP, _VP, ctypes.c_uint64,
                                          ctypes.c_int32, _VP, _VP, _VP, _VP]),
     "hg_plan_set_timing": (ctypes.c_int, [_VP, ctypes.c_int32]),
@@ -186,6 +187,13 @@ def hg_gs_run(plan: int, target_amp, init_phase=None, seed: int = 0, n_iter: int
                             None if nmse_out is None else _data_ptr(nmse_out), _stream(stream)), "hg_gs_run")
 
 
+def hg_ospr_run(plan: int, target_amp, n_subframes: int, n_iter: int = 0, seed: int = 0, bits_out=None,
+                nmse_out=None, stream=None):
+    """One-Step Phase-Retrieval for every item of the plan (see hologen.h)."""
+    _check(load().hg_ospr_run(plan, _ptr_array(target_amp), n_subframes, n_iter, seed, _ptr_array(bits_out),
+                              None if nmse_out is None else _data_ptr(nmse_out), _stream(stream)), "hg_ospr_run")
+
+
 def hg_gs_run_noalloc(height: int, width: int, quant_levels: int, target_amp, init_phase=None, seed: int = 0,
                       n_iter: int = 1, phase_out=None, level_out=None, nmse_out=None, stream=None):
     """GS for one Fourier hologram with no device allocation (static scratch; see hologen.h).
@@ -260,6 +268,9 @@ class Plan:
     def gs(self, target_amp, n_iter, init_phase=None, seed=0, phase_out=None, level_out=None, nmse_out=None,
            stream=None):
         hg_gs_run(self.handle, target_amp, init_phase, seed, n_iter, phase_out, level_out, nmse_out, stream)
+
+    def ospr(self, target_amp, n_subframes, n_iter=0, seed=0, bits_out=None, nmse_out=None, stream=None):
+        hg_ospr_run(self.handle, target_amp, n_subframes, n_iter, seed, bits_out, nmse_out, stream)
 
     def sync(self):
         hg_plan_sync(self.handle)

@@ -89,8 +89,9 @@ range_fn_t range_fn() {
 constexpr int kMaxItems = 256;
 
 // Kernel kinds for the timing facility.
-enum Kind { K_ROW_INIT = 0, K_ROW_GS, K_COL_GS, K_COL_NMSE, K_ROW_FFT, K_COL_FFT, K_NUM_KINDS };
-const char* const kKindNames[K_NUM_KINDS] = {"row_init", "row_gs", "col_gs", "col_nmse", "row_fft", "col_fft"};
+enum Kind { K_ROW_INIT = 0, K_ROW_GS, K_COL_GS, K_COL_NMSE, K_ROW_FFT, K_COL_FFT, K_ROW_OSPR, K_COL_OSPR, K_NUM_KINDS };
+const char* const kKindNames[K_NUM_KINDS] = {"row_init", "row_gs",   "col_gs",   "col_nmse",
+                                             "row_fft",  "col_fft",  "row_ospr", "col_ospr"};
 constexpr int kMaxLevels = 256;
 
 struct SizeClass {
@@ -101,6 +102,7 @@ struct SizeClass {
   float2* field = nullptr;       // [slot][plane][H][W]
   double* partials = nullptr;    // [slot][plane][3 * col_blocks]
   unsigned* counters = nullptr;  // [slot][plane]
+  float* acc = nullptr;          // [slot][H][W] OSPR accumulated intensity (allocated on first use)
   std::vector<float2*> cx, cy;   // per plane (Fresnel)
   int row_blocks() const { return (H + rk->rows - 1) / rk->rows; }
   int col_blocks() const { return (W + ck->cols - 1) / ck->cols; }
@@ -594,6 +596,71 @@ hg_status hg_gs_run(hg_plan* p, const float* const* target_amp, const float* con
       }
       a.iter = n_iter;
       if ((s = launch(p, K_COL_NMSE, c.ck->gs[0], gcol, c.ck->nt, c.ck->smem, a, st)) != HG_OK) return s;
+    }
+  }
+  return HG_OK;
+}
+
+hg_status hg_ospr_run(hg_plan* p, const float* const* target_amp, int32_t n_subframes, int32_t n_iter,
+                      uint64_t seed, uint32_t* const* bits_out, float* nmse_out, void* stream) {
+  if (!p) return fail(HG_ERR_INVALID_ARG, "plan is NULL");
+  if (n_subframes < 1 || n_subframes > 65535) return fail(HG_ERR_INVALID_ARG, "n_subframes must be 1..65535");
+  if (n_iter < 0 || n_iter > 10000) return fail(HG_ERR_INVALID_ARG, "n_iter must be 0..10000");
+  if (!target_amp) return fail(HG_ERR_INVALID_ARG, "target_amp is NULL");
+  if (p->P != 1) return fail(HG_ERR_INVALID_ARG, "OSPR needs a single-plane plan");
+  DeviceGuard g(p->device);
+  if (!g.ok) return fail(HG_ERR_CUDA, "cannot select device %d", p->device);
+  hg_status s;
+  for (int i = 0; i < p->n_items; ++i) {
+    const size_t px = (size_t)p->H[i] * p->W[i];
+    if ((s = check_ptr(p, target_amp[i], px * 4, 4, "target_amp", i)) != HG_OK) return s;
+    const size_t words = (size_t)n_subframes * p->H[i] * ((p->W[i] + 31) / 32);
+    if (bits_out && bits_out[i] && (s = check_ptr(p, bits_out[i], words * 4, 4, "bits_out", i)) != HG_OK) return s;
+  }
+  if (nmse_out && (s = check_ptr(p, nmse_out, (size_t)p->n_items * n_subframes * 4, 4, "nmse_out", 0)) != HG_OK)
+    return s;
+  for (SizeClass& c : p->classes)
+    if (!c.acc && (s = p->alloc(&c.acc, c.items.size() * (size_t)c.H * c.W, "OSPR intensity buffer")) != HG_OK)
+      return s;
+
+  cudaStream_t st = (cudaStream_t)stream;
+  for (const SizeClass& c : p->classes) {
+    for (size_t c0 = 0; c0 < c.items.size(); c0 += hg::kMaxBatch) {
+      const int nb = (int)std::min<size_t>(hg::kMaxBatch, c.items.size() - c0);
+      hg::PassArgs a{};
+      fill_common(p, c, 0, a);
+      a.n_levels = 2;
+      a.n_items = nb;
+      a.acc = c.acc;
+      a.nmse_stride = n_subframes;
+      a.seed = seed;
+      for (int k = 0; k < nb; ++k) {
+        const int item = c.items[c0 + k];
+        a.item_index[k] = item;
+        a.class_slot[k] = (int)(c0 + k);
+        a.target[k] = target_amp[item];
+        a.bits[k] = bits_out ? bits_out[item] : nullptr;
+      }
+      hg::PassArgs ag = a;  // binary GS refinements inside a subframe: no NMSE, no bits
+      ag.nmse = nullptr;
+      a.nmse = nmse_out;
+      const dim3 grow(c.row_blocks(), nb), gcol(c.col_blocks(), nb);
+      const int rs = c.rk->smem_ospr;
+      a.iter = 0;
+      if ((s = launch(p, K_COL_OSPR, c.ck->ospr[0], gcol, c.ck->nt, c.ck->smem, a, st)) != HG_OK) return s;
+      for (int sf = 0; sf < n_subframes; ++sf) {
+        a.iter = sf;
+        if ((s = launch(p, K_ROW_OSPR, c.rk->ospr[n_iter == 0], grow, c.rk->nt, rs, a, st)) != HG_OK) return s;
+        for (int it = 0; it < n_iter; ++it) {
+          if ((s = launch(p, K_COL_GS, c.ck->gs[1], gcol, c.ck->nt, c.ck->smem, ag, st)) != HG_OK) return s;
+          if ((s = launch(p, K_ROW_OSPR, c.rk->ospr[it == n_iter - 1], grow, c.rk->nt, rs, a, st)) != HG_OK)
+            return s;
+        }
+        a.iter = sf + 1;
+        a.acc_read = sf > 0;
+        const int variant = sf + 1 < n_subframes ? 1 : 2;
+        if ((s = launch(p, K_COL_OSPR, c.ck->ospr[variant], gcol, c.ck->nt, c.ck->smem, a, st)) != HG_OK) return s;
+      }
     }
   }
   return HG_OK;

@@ -81,6 +81,10 @@ struct PassArgs {
   uint8_t* level_out[kMaxBatch];
   const float2* in[kMaxBatch];  // bare propagation input
   float2* out[kMaxBatch];       // bare propagation output
+  // OSPR
+  float* acc;                   // class accumulated-intensity buffer: item k at acc + k * H * W
+  int acc_read;                 // 1: add to the stored sum, 0: start it
+  uint32_t* bits[kMaxBatch];    // [S][H][ceil(W/32)] LSB-first hologram bits, or nullptr
 };
 
 // ---------------------------------------------------------------- pointwise pieces
@@ -392,6 +396,147 @@ __global__ void __launch_bounds__(ColCfg<H>::NT) k_col_fft(const __grid_constant
       if (POST) x = c_mulc(x, c_mul(__ldg(&a.cx[col]), __ldg(&a.cy[n])));
       f[(size_t)n * W + col] = x;
     }
+  });
+}
+
+// ---------------------------------------------------------------- OSPR passes
+//
+// One-Step Phase-Retrieval (Cable, Buckley et al.; section "Algorithm Libraries",
+// HoloGenAlgOSPRCuda).  Subframe s of target t: E = A exp(2 pi i u), u from Philox4x32-10 (counter
+// (p, s, 0, 0), key (seed_lo, seed_hi ^ t)); h = binary(conj(c) F^-1(E)); I_acc += |F(h c)|^2;
+// NMSE(I_acc, A^2) after each subframe.  Per subframe the field crosses HBM in two passes:
+//   column pass: [finish s-1: forward column FFTs, I_acc += |R|^2, NMSE partials]
+//                [start s: random-phase field, inverse column FFTs] -> field
+//   row pass:    inverse row FFTs, conj chirp, binarise (bits out), chirp, forward row FFTs -> field
+
+namespace ospr {
+__device__ __forceinline__ float2 random_field(uint32_t p, int s, uint64_t seed, int target, float amp) {
+  const uint4 x = philox4x32_10(make_uint4(p, (uint32_t)s, 0u, 0u),
+                                make_uint2((uint32_t)seed, (uint32_t)(seed >> 32) ^ (uint32_t)target));
+  const float u2 = (float)(x.x >> 8) * (1.0f / 8388608.0f);  // 2u
+  float sn, cs;
+  sincospif(u2, &sn, &cs);
+  return make_float2(amp * cs, amp * sn);
+}
+}  // namespace ospr
+
+// FINISH: the field holds rowFFT(h_{s-1} c); accumulate its replay intensity (ACC_READ: add to the
+// stored sum, else start it) and write NMSE[s-1].  START: build subframe s and inverse-transform it.
+template <int H, bool FINISH, bool START>
+__global__ void __launch_bounds__(ColCfg<H>::NT) k_col_ospr(const __grid_constant__ PassArgs a) {
+  using K = ColCfg<H>;
+  using G = typename K::G;
+  extern __shared__ float2 sm[];
+  const int t = threadIdx.x, k = blockIdx.y;
+  const int col0 = blockIdx.x * K::C;
+  const int W = a.W;
+  const int slot = a.class_slot[k];
+  float2* f = a.field + (size_t)slot * H * W;
+  float* acc = a.acc + (size_t)slot * H * W;
+  const float* A = a.target[k];
+  float2 v[K::V];
+  float s_it = 0.f, s_ii = 0.f, s_tt = 0.f;
+  if (FINISH) {
+    for_each_slot<G, K::RB>(t, [&](int s, int b, int n) {
+      const int col = col0 + b;
+      v[s] = col < W ? f[(size_t)n * W + col] : make_float2(0.f, 0.f);
+    });
+    FftRun<G, false, 1, typename K::Fwd>::run(v, sm, t, a.tw_col);
+    for_each_slot<G, RLast<typename K::Fwd>::value>(t, [&](int s, int b, int n) {
+      const int col = col0 + b;
+      if (col < W) {
+        const size_t p = (size_t)n * W + col;
+        const float2 r = v[s];
+        float i2 = fmaf(r.x, r.x, r.y * r.y);
+        if (a.acc_read) i2 += acc[p];
+        acc[p] = i2;
+        const float amp = __ldg(&A[p]);
+        const float tt = amp * amp;
+        s_it = fmaf(i2, tt, s_it);
+        s_ii = fmaf(i2, i2, s_ii);
+        s_tt = fmaf(tt, tt, s_tt);
+      }
+    });
+  }
+  if (START) {
+    if (FINISH) __syncthreads();  // the forward transform's last exchange is done with sm
+    for_each_slot<G, RFirst<typename K::Inv>::value>(t, [&](int s, int b, int n) {
+      const int col = col0 + b;
+      float2 e = make_float2(0.f, 0.f);
+      if (col < W) {
+        const uint32_t p = (uint32_t)((size_t)n * W + col);
+        e = ospr::random_field(p, a.iter, a.seed, a.item_index[k], __ldg(&A[p]));
+      }
+      v[s] = e;
+    });
+    // the inverse runs the reversed plan: its first radix is the forward plan's last
+    FftRun<G, true, 1, typename K::Inv>::run(v, sm, t, a.tw_col);
+    for_each_slot<G, K::RB>(t, [&](int s, int b, int n) {
+      const int col = col0 + b;
+      if (col < W) f[(size_t)n * W + col] = v[s];
+    });
+  }
+  if (FINISH) {
+    float* dst = a.nmse ? a.nmse + (size_t)a.item_index[k] * a.nmse_stride + (a.iter - 1) : nullptr;
+    nmse_reduce(s_it, s_ii, s_tt, a.partials + (size_t)slot * 3 * gridDim.x, a.counters + slot, gridDim.x, dst);
+  }
+}
+
+// OSPR row pass: inverse row FFTs, conj chirp, binary projection (bits written LSB-first, 32 pixels
+// per word, when BITS and a bits pointer is set), chirp, forward row FFTs.
+template <int W, bool BITS>
+__global__ void __launch_bounds__(RowCfg<W>::NT) k_row_ospr(const __grid_constant__ PassArgs a) {
+  using K = RowCfg<W>;
+  using G = typename K::G;
+  constexpr int WORDS = (W + 31) / 32;
+  extern __shared__ float2 sm[];
+  unsigned char* qs = reinterpret_cast<unsigned char*>(sm + K::ROWS * W);  // [ROWS][W] decisions
+  const int t = threadIdx.x, k = blockIdx.y;
+  const int row0 = blockIdx.x * K::ROWS;
+  const int H = a.H;
+  float2* f = a.field + (size_t)a.class_slot[k] * H * W;
+  uint32_t* bits = BITS ? a.bits[k] : nullptr;
+  float2 v[K::V];
+  for_each_slot<G, K::RE>(t, [&](int s, int b, int n) {
+    const int row = row0 + b;
+    v[s] = row < H ? f[(size_t)row * W + n] : make_float2(0.f, 0.f);
+  });
+  FftRun<G, true, 1, typename K::Inv>::run(v, sm, t, a.tw_row);
+  for_each_slot<G, K::RM>(t, [&](int s, int b, int n) {
+    const int row = row0 + b;
+    float2 g = v[s];
+    float2 c = make_float2(1.f, 0.f);
+    if (a.cx && row < H) {
+      c = c_mul(__ldg(&a.cx[n]), __ldg(&a.cy[row]));
+      g = c_mulc(g, c);
+    }
+    const int q = (g.x < 0.f || (g.x == 0.f && g.y > 0.f)) ? 1 : 0;
+    if (BITS) qs[b * W + n] = (unsigned char)q;
+    float2 h = make_float2(q ? -1.f : 1.f, 0.f);
+    if (a.cx) h = c_mul(h, c);
+    v[s] = row < H ? h : make_float2(0.f, 0.f);
+  });
+  if (BITS) {
+    __syncthreads();
+    if (bits) {
+      uint32_t* dst = bits + (size_t)a.iter * H * WORDS;
+      for (int w = t; w < K::ROWS * WORDS; w += K::NT) {
+        const int b = w / WORDS, word = w % WORDS;
+        const int row = row0 + b;
+        if (row >= H) continue;
+        uint32_t x = 0;
+        for (int i = 0; i < 32; ++i) {
+          const int n = word * 32 + i;
+          if (n < W) x |= (uint32_t)qs[b * W + n] << i;
+        }
+        dst[(size_t)row * WORDS + word] = x;
+      }
+    }
+  }
+  FftRun<G, false, 1, typename K::Fwd>::run(v, sm, t, a.tw_row);
+  for_each_slot<G, K::RE>(t, [&](int s, int b, int n) {
+    const int row = row0 + b;
+    if (row < H) f[(size_t)row * W + n] = v[s];
   });
 }
 

@@ -13,6 +13,8 @@ struct RowKernels {
   const void* init;         // k_row_init
   const void* gs[2];        // k_row_gs<OUT = false / true>
   const void* fft[2][2];    // k_row_fft<INV><PRE>
+  const void* ospr[2];      // k_row_ospr<BITS = false / true>
+  int smem_ospr;            // dynamic shared memory of k_row_ospr (field tile + bit decisions)
   void (*set_attrs)();      // raises the dynamic shared-memory limit on the current device
 };
 
@@ -22,6 +24,7 @@ struct ColKernels {
   int smem;
   const void* gs[2];        // k_col_gs<REPLACE = false / true>
   const void* fft[2][2];    // k_col_fft<INV><POST>
+  const void* ospr[3];      // k_col_ospr: [0] start only, [1] finish + start, [2] finish only
   void (*set_attrs)();
 };
 

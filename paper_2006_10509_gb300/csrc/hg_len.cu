@@ -29,6 +29,9 @@ RowKernels make_row() {
   r.fft[0][1] = (const void*)&k_row_fft<N, false, true>;
   r.fft[1][0] = (const void*)&k_row_fft<N, true, false>;
   r.fft[1][1] = (const void*)&k_row_fft<N, true, true>;
+  r.ospr[0] = (const void*)&k_row_ospr<N, false>;
+  r.ospr[1] = (const void*)&k_row_ospr<N, true>;
+  r.smem_ospr = K::SMEM + K::ROWS * N;
   return r;
 }
 
@@ -45,6 +48,9 @@ ColKernels make_col() {
   c.fft[0][1] = (const void*)&k_col_fft<N, false, true>;
   c.fft[1][0] = (const void*)&k_col_fft<N, true, false>;
   c.fft[1][1] = (const void*)&k_col_fft<N, true, true>;
+  c.ospr[0] = (const void*)&k_col_ospr<N, false, true>;
+  c.ospr[1] = (const void*)&k_col_ospr<N, true, true>;
+  c.ospr[2] = (const void*)&k_col_ospr<N, true, false>;
   return c;
 }
 
@@ -56,6 +62,8 @@ void set_row_attrs(const RowKernels& r) {
   allow_smem(&k_row_fft<HG_LEN, false, true>, r.smem);
   allow_smem(&k_row_fft<HG_LEN, true, false>, r.smem);
   allow_smem(&k_row_fft<HG_LEN, true, true>, r.smem);
+  allow_smem(&k_row_ospr<HG_LEN, false>, r.smem_ospr);
+  allow_smem(&k_row_ospr<HG_LEN, true>, r.smem_ospr);
 }
 
 void set_col_attrs(const ColKernels& c) {
@@ -65,6 +73,9 @@ void set_col_attrs(const ColKernels& c) {
   allow_smem(&k_col_fft<HG_LEN, false, true>, c.smem);
   allow_smem(&k_col_fft<HG_LEN, true, false>, c.smem);
   allow_smem(&k_col_fft<HG_LEN, true, true>, c.smem);
+  allow_smem(&k_col_ospr<HG_LEN, false, true>, c.smem);
+  allow_smem(&k_col_ospr<HG_LEN, true, true>, c.smem);
+  allow_smem(&k_col_ospr<HG_LEN, true, false>, c.smem);
 }
 
 }  // namespace

@@ -73,7 +73,10 @@ def test_null_plan_calls(hg):
     assert lib.hg_plan_sync(None) == 1
     assert lib.hg_propagate(None, 0, 1, None, None, None) == 1
     assert lib.hg_gs_run(None, None, None, 0, 1, None, None, None, None) == 1
+    assert lib.hg_ospr_run(None, None, 1, 0, 0, None, None, None) == 1
     assert "NULL" in hg.hg_last_error()
+    assert lib.hg_gs_run_noalloc(4096, 4096, 0, None, None, 0, 1, None, None, None, None) == 2
+    assert "1048576" in hg.hg_last_error()
 
 
 def test_product_path_has_no_oracle_or_fallback():

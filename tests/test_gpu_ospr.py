@@ -1,0 +1,85 @@
+"""GPU parity of One-Step Phase-Retrieval (hg_ospr_run) against the FP64 oracle.
+
+Every subframe starts from its own Philox random phase, which both sides draw from the same
+counter-based definition, so with no refinement iterations each subframe's hologram is compared
+directly: bits equal on >= 99.9 % of pixels, every mismatch at a pre-binarisation phase within
+1e-4 rad of a level boundary (Re g = 0).  The NMSE of the accumulated replay after every subframe is
+within 1 % of the oracle's.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import optics, ospr as oospr
+from tests.helpers import check_levels, check_nmse, cuda_device
+
+LAM, PITCH = 532e-9, 8e-6
+
+
+def _run(hg, dev, targets, s, n_iter=0, seed=3000, z=None):
+    import torch
+
+    hs = [t.shape[0] for t in targets]
+    ws = [t.shape[1] for t in targets]
+    kw = dict(propagation=hg.HG_FRESNEL, wavelength_m=LAM, pitch_m=PITCH, z_m=[z]) if z else {}
+    with hg.Plan(hs, ws, quant_levels=2, **kw) as plan:
+        ta = [torch.from_numpy(t).to(dev) for t in targets]
+        bits = [torch.zeros((s, h, (w + 31) // 32), dtype=torch.int32, device=dev) for h, w in zip(hs, ws)]
+        nm = torch.zeros((len(targets), s), dtype=torch.float32, device=dev)
+        plan.ospr(ta, s, n_iter, seed, bits_out=bits, nmse_out=nm)
+        plan.sync()
+        return [b.cpu().numpy().view(np.uint32) for b in bits], nm.cpu().numpy()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("h, w, s, z", [(64, 64, 4, None), (30, 120, 3, None), (120, 64, 3, 0.05),
+                                        (1080, 1920, 3, None)])
+def test_ospr_subframes_match_oracle(h, w, s, z):
+    import paper_2006_10509_gb300 as hg
+
+    dev = cuda_device()
+    targets = [synth.symmetrise(synth.blur_target(h, w, 2.0, seed=3001 + k)) for k in range(2)]
+    bits, nm = _run(hg, dev, targets, s, z=z)
+    c = optics.chirp(h, w, LAM, PITCH, z) if z else None
+    for t, a in enumerate(targets):
+        a64 = a.astype(np.float64)
+        i_acc = np.zeros((h, w))
+        curve = []
+        for sf in range(s):
+            ref = oospr.ospr_subframe(a64, sf, t, 3000, 0, c)
+            q_gpu = oospr.unpack_bits(bits[t][sf], w)
+            check_levels(q_gpu, ref["q"], ref["g"], 2)
+            # replay of the GPU's own hologram (teacher forcing for the accumulated NMSE)
+            from oracle.fft import fft2
+            from oracle.metrics import nmse
+
+            hh = 1.0 - 2.0 * q_gpu
+            i_acc += np.abs(fft2(hh if c is None else hh * c)) ** 2
+            curve.append(nmse(i_acc, a64 * a64))
+        check_nmse(nm[t], curve, rtol=1e-3)
+
+
+@pytest.mark.gpu
+def test_ospr_with_refinement_iterations():
+    import paper_2006_10509_gb300 as hg
+
+    dev = cuda_device()
+    a = synth.symmetrise(synth.blur_target(64, 120, 2.0, seed=7))
+    bits, nm = _run(hg, dev, [a], 4, n_iter=2, seed=11)
+    ref = oospr.ospr(a.astype(np.float64), 4, 0, 11, n_iter=2)
+    check_nmse(nm[0], ref["nmse"])
+    agree = np.mean([np.mean(oospr.unpack_bits(bits[0][k], 120) == ref["q"][k]) for k in range(4)])
+    assert agree > 0.99
+
+
+@pytest.mark.gpu
+def test_ospr_nmse_falls_and_bits_are_packed():
+    import paper_2006_10509_gb300 as hg
+
+    dev = cuda_device()
+    a = synth.symmetrise(synth.blur_target(256, 256, 2.0, seed=5))
+    bits, nm = _run(hg, dev, [a], 16)
+    assert nm[0, 15] < nm[0, 3] < nm[0, 0]
+    assert bits[0].shape == (16, 256, 8)
+    ones = np.mean([np.mean(oospr.unpack_bits(bits[0][k], 256)) for k in range(16)])
+    assert 0.3 < ones < 0.7
