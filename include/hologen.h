@@ -145,6 +145,38 @@ HG_API hg_status hg_ospr_run(hg_plan* plan, const float* const* target_amp, int3
                              uint64_t seed, uint32_t* const* bits_out, float* nmse_out, void* stream);
 
 /*
+ * Gradient-descent hologram optimisation (Wirtinger calculus; no counterpart in the paper, which
+ * offers GS, SA, DS and OSPR): one Adam step on the phase phi of every item, for a loss over the
+ * plan's P replay planes (Fresnel distances z_m, or one Fourier plane):
+ *   U_p = F(exp(i phi) c_p),  I_p = |U_p|^2,  s_p = sum(I_p T_p) / sum(I_p^2),
+ *   L_p = sum((s_p I_p - T_p)^2) / sum(T_p^2),  L = (1/P) sum_p L_p,
+ *   dL/dphi = 2 Im(g conj(exp(i phi))),  g = sum_p conj(c_p) F^-1((2/P) s_p (s_p I_p - T_p)/sum(T_p^2) U_p)
+ * (s_p is optimal, so it is held fixed in the derivative), then Adam (Kingma & Ba):
+ *   m = b1 m + (1-b1) grad;  v = b2 v + (1-b2) grad^2;
+ *   phi -= lr (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps).
+ *  phase[k]          float32 [H][W], updated in place (unwrapped)
+ *  target_int[k*P+p] float32 [H][W] target intensity T_p (FFT order)
+ *  adam_m, adam_v    per item float32 [H][W] moments (zero before step 1), updated in place
+ *  step              1-based step count
+ *  loss_out          NULL or device float32 [n_items][P + 1]: L_p per plane, then L (before the update)
+ *  grad_out          NULL, or per item NULL / float32 [H][W]: dL/dphi at the input phase
+ * The plan must be continuous-phase (quant_levels 0).  The per-plane row-FFT fields of the forward
+ * transform are kept in the plan workspace as the checkpoint the adjoint pass recomputes U_p from.
+ */
+HG_API hg_status hg_gd_step(hg_plan* plan, float* const* phase, const float* const* target_int,
+                            float* const* adam_m, float* const* adam_v, int32_t step, float lr, float beta1,
+                            float beta2, float eps, float* loss_out, float* const* grad_out, void* stream);
+
+/* The two halves of hg_gd_step without the update, for autograd front ends: hg_gd_forward writes
+ * loss_out and keeps the checkpoint; hg_gd_backward (after exactly one hg_gd_forward with the same
+ * phase and targets) writes grad_out[k] = grad_scale * dL/dphi (grad_scale: NULL = 1, or a device
+ * float32 scalar). */
+HG_API hg_status hg_gd_forward(hg_plan* plan, float* const* phase, const float* const* target_int,
+                               float* loss_out, void* stream);
+HG_API hg_status hg_gd_backward(hg_plan* plan, float* const* phase, const float* const* target_int,
+                                const float* grad_scale, float* const* grad_out, void* stream);
+
+/*
  * Gerchberg-Saxton for ONE Fourier hologram without allocating device memory.  The paper has no
  * counterpart: this exists for callers that cannot call cudaMalloc -- code running inside a memory
  * arena it does not own, plug-ins whose host forbids allocation after start-up, real-time loops in

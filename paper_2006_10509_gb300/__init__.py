@@ -22,7 +22,8 @@ __all__ = [
     "HologenError", "lib_path", "load", "hg_plan_create", "hg_plan_destroy", "hg_plan_sync",
     "hg_propagate", "hg_gs_run", "hg_status_string", "hg_last_error", "hg_supported_length", "Plan",
     "hg_plan_set_timing", "hg_plan_reset_timing", "hg_plan_kernel_time", "hg_kernel_kind_name",
-    "hg_plan_launch_count", "hg_gs_run_noalloc", "hg_ospr_run",
+    "hg_plan_launch_count", "hg_gs_run_noalloc", "hg_ospr_run", "hg_gd_step", "hg_gd_forward",
+    "hg_gd_backward", "hologram_loss",
 ]
 
 HG_OK, HG_ERR_INVALID_ARG, HG_ERR_UNSUPPORTED_SIZE, HG_ERR_OUT_OF_MEMORY = 0, 1, 2, 3
@@ -68,6 +69,10 @@ _SIGNATURES = {
     "hg_propagate": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32, _PP, _PP, _VP]),
     "hg_gs_run": (ctypes.c_int, [_VP, _PP, _PP, ctypes.c_uint64, ctypes.c_int32, _PP, _PP, _VP, _VP]),
     "hg_ospr_run": (ctypes.c_int, [_VP, _PP, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64, _PP, _VP, _VP]),
+    "hg_gd_step": (ctypes.c_int, [_VP, _PP, _PP, _PP, _PP, ctypes.c_int32, ctypes.c_float, ctypes.c_float,
+                                  ctypes.c_float, ctypes.c_float, _VP, _PP, _VP]),
+    "hg_gd_forward": (ctypes.c_int, [_VP, _PP, _PP, _VP, _VP]),
+    "hg_gd_backward": (ctypes.c_int, [_VP, _PP, _PP, _VP, _PP, _VP]),
     "hg_gs_run_noalloc": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _VP, _VP, ctypes.c_uint64,
                                          ctypes.c_int32, _VP, _VP, _VP, _VP]),
     "hg_plan_set_timing": (ctypes.c_int, [_VP, ctypes.c_int32]),
@@ -194,6 +199,54 @@ def hg_ospr_run(plan: int, target_amp, n_subframes: int, n_iter: int = 0, seed: 
                               None if nmse_out is None else _data_ptr(nmse_out), _stream(stream)), "hg_ospr_run")
 
 
+def hg_gd_step(plan: int, phase, target_int, adam_m, adam_v, step: int, lr: float = 0.05, beta1: float = 0.9,
+               beta2: float = 0.999, eps: float = 1e-8, loss_out=None, grad_out=None, stream=None):
+    """One Adam step of gradient-descent hologram optimisation for every item (see hologen.h)."""
+    _check(load().hg_gd_step(plan, _ptr_array(phase), _ptr_array(target_int), _ptr_array(adam_m), _ptr_array(adam_v),
+                             step, lr, beta1, beta2, eps, None if loss_out is None else _data_ptr(loss_out),
+                             _ptr_array(grad_out), _stream(stream)), "hg_gd_step")
+
+
+def hg_gd_forward(plan: int, phase, target_int, loss_out=None, stream=None):
+    _check(load().hg_gd_forward(plan, _ptr_array(phase), _ptr_array(target_int),
+                                None if loss_out is None else _data_ptr(loss_out), _stream(stream)), "hg_gd_forward")
+
+
+def hg_gd_backward(plan: int, phase, target_int, grad_out, grad_scale=None, stream=None):
+    _check(load().hg_gd_backward(plan, _ptr_array(phase), _ptr_array(target_int),
+                                 None if grad_scale is None else _data_ptr(grad_scale), _ptr_array(grad_out),
+                                 _stream(stream)), "hg_gd_backward")
+
+
+def hologram_loss(plan: "Plan", phase, target_int):
+    """Differentiable multi-plane hologram loss L(phase) (mean over planes of the optimal-scale
+    intensity NMSE) for a one-item plan; the backward pass is the library's hand-written adjoint.
+
+    ``phase``: float32 [H][W] CUDA tensor (requires_grad as usual); ``target_int``: P float32 [H][W]
+    CUDA tensors.  One backward per forward (the forward's per-plane fields are the checkpoint).
+    """
+    import torch
+
+    class _HologramLoss(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, ph):
+            ph = ph.detach().contiguous()
+            loss = torch.empty((plan.n_planes + 1,), dtype=torch.float32, device=ph.device)
+            hg_gd_forward(plan.handle, [ph], list(target_int), loss)
+            ctx.save_for_backward(ph)
+            return loss[plan.n_planes].clone()
+
+        @staticmethod
+        def backward(ctx, grad_loss):
+            (ph,) = ctx.saved_tensors
+            grad = torch.empty_like(ph)
+            gs = grad_loss.detach().reshape(1).to(torch.float32).contiguous()
+            hg_gd_backward(plan.handle, [ph], list(target_int), [grad], gs)
+            return grad
+
+    return _HologramLoss.apply(phase)
+
+
 def hg_gs_run_noalloc(height: int, width: int, quant_levels: int, target_amp, init_phase=None, seed: int = 0,
                       n_iter: int = 1, phase_out=None, level_out=None, nmse_out=None, stream=None):
     """GS for one Fourier hologram with no device allocation (static scratch; see hologen.h).
@@ -271,6 +324,11 @@ class Plan:
 
     def ospr(self, target_amp, n_subframes, n_iter=0, seed=0, bits_out=None, nmse_out=None, stream=None):
         hg_ospr_run(self.handle, target_amp, n_subframes, n_iter, seed, bits_out, nmse_out, stream)
+
+    def gd_step(self, phase, target_int, adam_m, adam_v, step, lr=0.05, beta1=0.9, beta2=0.999, eps=1e-8,
+                loss_out=None, grad_out=None, stream=None):
+        hg_gd_step(self.handle, phase, target_int, adam_m, adam_v, step, lr, beta1, beta2, eps, loss_out, grad_out,
+                   stream)
 
     def sync(self):
         hg_plan_sync(self.handle)

@@ -89,9 +89,14 @@ range_fn_t range_fn() {
 constexpr int kMaxItems = 256;
 
 // Kernel kinds for the timing facility.
-enum Kind { K_ROW_INIT = 0, K_ROW_GS, K_COL_GS, K_COL_NMSE, K_ROW_FFT, K_COL_FFT, K_ROW_OSPR, K_COL_OSPR, K_NUM_KINDS };
-const char* const kKindNames[K_NUM_KINDS] = {"row_init", "row_gs",   "col_gs",   "col_nmse",
-                                             "row_fft",  "col_fft",  "row_ospr", "col_ospr"};
+enum Kind {
+  K_ROW_INIT = 0, K_ROW_GS, K_COL_GS, K_COL_NMSE, K_ROW_FFT, K_COL_FFT, K_ROW_OSPR, K_COL_OSPR,
+  K_ROW_MP_INIT, K_ROW_MP, K_ROW_GD_FWD, K_COL_GD_FWD, K_COL_GD_BWD, K_ROW_GD_BWD, K_AMP_ENERGY, K_NUM_KINDS
+};
+const char* const kKindNames[K_NUM_KINDS] = {"row_init",   "row_gs",     "col_gs",     "col_nmse",  "row_fft",
+                                             "col_fft",    "row_ospr",   "col_ospr",   "row_mp_init", "row_mp",
+                                             "row_gd_fwd", "col_gd_fwd", "col_gd_bwd", "row_gd_bwd",
+                                             "amp_energy"};
 constexpr int kMaxLevels = 256;
 
 struct SizeClass {
@@ -103,6 +108,9 @@ struct SizeClass {
   double* partials = nullptr;    // [slot][plane][3 * col_blocks]
   unsigned* counters = nullptr;  // [slot][plane]
   float* acc = nullptr;          // [slot][H][W] OSPR accumulated intensity (allocated on first use)
+  float* plane_val = nullptr;    // [slot][plane] per-plane NMSE / loss
+  unsigned* plane_counters = nullptr;  // [slot]
+  double* stats = nullptr;       // [slot][plane][4] gradient-descent loss statistics
   std::vector<float2*> cx, cy;   // per plane (Fresnel)
   int row_blocks() const { return (H + rk->rows - 1) / rk->rows; }
   int col_blocks() const { return (W + ck->cols - 1) / ck->cols; }
@@ -296,7 +304,41 @@ void fill_common(const hg_plan* p, const SizeClass& c, int plane, hg::PassArgs& 
   a.field = c.field;
   a.partials = c.partials;
   a.counters = c.counters;
+  a.n_planes = p->P;
+  for (int q = 0; q < p->P; ++q) {
+    a.cxp[q] = p->propagation == HG_FRESNEL ? c.cx[q] : nullptr;
+    a.cyp[q] = p->propagation == HG_FRESNEL ? c.cy[q] : nullptr;
+  }
+  a.plane_val = c.plane_val;
+  a.plane_counters = c.plane_counters;
+  a.stats = c.stats;
 }
+
+}  // namespace
+
+// Per (item, plane) amplitude energy of the targets: stats[4 sp + 3] = 1 / sqrt(sum A^2)
+// (multi-plane GS weights each plane's back-propagated field by it).  blockIdx.y = item * P + plane.
+__global__ void k_amp_energy(const __grid_constant__ hg::PassArgs a) {
+  const int P = a.n_planes > 1 ? a.n_planes : 1;
+  const int k = blockIdx.y / P, p = blockIdx.y % P;
+  const int sp = a.class_slot[k] * P + p;
+  const float* A = a.target[k * P + p];
+  const size_t n = (size_t)a.H * a.W;
+  float e = 0.f;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const float x = __ldg(&A[i]);
+    e = fmaf(x, x, e);
+  }
+  double tot[3];
+  if (hg::block_totals(e, 0.f, 0.f, a.partials + (size_t)sp * 3 * gridDim.x, a.counters + sp, gridDim.x, tot) &&
+      threadIdx.x == 0)
+    a.stats[(size_t)sp * 4 + 3] = tot[0] > 0.0 ? 1.0 / sqrt(tot[0]) : 1.0;
+}
+
+namespace {
+
+// items per launch: (item, plane) pairs of one launch must fit the argument block
+int chunk_items(const hg_plan* p) { return std::max(1, hg::kMaxBatch / p->P); }
 
 }  // namespace
 
@@ -432,6 +474,12 @@ hg_status hg_plan_create(const hg_plan_desc* d, hg_plan** out) {
     if ((s = p->alloc(&c.partials, n * 3 * c.col_blocks(), "reduction scratch")) != HG_OK) return bail(s);
     if ((s = p->alloc(&c.counters, n, "reduction counters")) != HG_OK) return bail(s);
     if (cudaMemset(c.counters, 0, n * sizeof(unsigned)) != cudaSuccess) return bail(cuda_fail(cudaGetLastError(), "memset"));
+    if ((s = p->alloc(&c.plane_val, n, "plane scratch")) != HG_OK) return bail(s);
+    if ((s = p->alloc(&c.plane_counters, c.items.size(), "plane counters")) != HG_OK) return bail(s);
+    if (cudaMemset(c.plane_counters, 0, c.items.size() * sizeof(unsigned)) != cudaSuccess)
+      return bail(cuda_fail(cudaGetLastError(), "memset"));
+    if ((s = p->alloc(&c.stats, n * 4, "loss statistics")) != HG_OK) return bail(s);
+    if (cudaMemset(c.stats, 0, n * 4 * sizeof(double)) != cudaSuccess) return bail(cuda_fail(cudaGetLastError(), "memset"));
     for (int pl = 0; pl < p->P; ++pl) {
       float2 *cx = nullptr, *cy = nullptr;
       if (p->propagation == HG_FRESNEL) {
@@ -536,7 +584,6 @@ hg_status hg_gs_run(hg_plan* p, const float* const* target_amp, const float* con
   if (!p) return fail(HG_ERR_INVALID_ARG, "plan is NULL");
   if (n_iter < 0 || n_iter > 1000000) return fail(HG_ERR_INVALID_ARG, "n_iter must be 0..1000000");
   if (!target_amp) return fail(HG_ERR_INVALID_ARG, "target_amp is NULL");
-  if (p->P != 1) return fail(HG_ERR_INVALID_ARG, "multi-plane GS is not available in this build");
   if (level_out && p->levels == 0) {
     for (int i = 0; i < p->n_items; ++i)
       if (level_out[i]) return fail(HG_ERR_INVALID_ARG, "level_out needs a quantised plan");
@@ -546,7 +593,8 @@ hg_status hg_gs_run(hg_plan* p, const float* const* target_amp, const float* con
   hg_status s;
   for (int i = 0; i < p->n_items; ++i) {
     const size_t px = (size_t)p->H[i] * p->W[i];
-    if ((s = check_ptr(p, target_amp[i], px * 4, 4, "target_amp", i)) != HG_OK) return s;
+    for (int q = 0; q < p->P; ++q)
+      if ((s = check_ptr(p, target_amp[i * p->P + q], px * 4, 4, "target_amp", i * p->P + q)) != HG_OK) return s;
     if (init_phase && init_phase[i] && (s = check_ptr(p, init_phase[i], px * 4, 4, "init_phase", i)) != HG_OK)
       return s;
     if (phase_out && phase_out[i] && (s = check_ptr(p, phase_out[i], px * 4, 4, "phase_out", i)) != HG_OK) return s;
@@ -556,9 +604,11 @@ hg_status hg_gs_run(hg_plan* p, const float* const* target_amp, const float* con
     return s;
 
   cudaStream_t st = (cudaStream_t)stream;
+  const int P = p->P;
+  const int chunk = chunk_items(p);
   for (const SizeClass& c : p->classes) {
-    for (size_t c0 = 0; c0 < c.items.size(); c0 += hg::kMaxBatch) {
-      const int nb = (int)std::min<size_t>(hg::kMaxBatch, c.items.size() - c0);
+    for (size_t c0 = 0; c0 < c.items.size(); c0 += chunk) {
+      const int nb = (int)std::min<size_t>(chunk, c.items.size() - c0);
       hg::PassArgs a{};
       fill_common(p, c, 0, a);
       a.n_items = nb;
@@ -569,8 +619,34 @@ hg_status hg_gs_run(hg_plan* p, const float* const* target_amp, const float* con
         const int item = c.items[c0 + k];
         a.item_index[k] = item;
         a.class_slot[k] = (int)(c0 + k);
-        a.target[k] = target_amp[item];
+        for (int q = 0; q < P; ++q) a.target[k * P + q] = target_amp[item * P + q];
         a.phase_in[k] = init_phase ? init_phase[item] : nullptr;
+      }
+      if (P > 1) {
+        // multi-plane GS: averaged projections over the P planes
+        const dim3 grow(c.row_blocks(), nb), gcol(c.col_blocks(), nb * P);
+        hg::PassArgs a0 = a, ao = a;
+        for (int k = 0; k < nb; ++k) {
+          const int item = c.items[c0 + k];
+          ao.phase_out[k] = phase_out ? phase_out[item] : nullptr;
+          ao.level_out[k] = level_out ? level_out[item] : nullptr;
+          if (n_iter == 0) {
+            a0.phase_out[k] = ao.phase_out[k];
+            a0.level_out[k] = ao.level_out[k];
+          }
+        }
+        if ((s = launch(p, K_AMP_ENERGY, (const void*)&k_amp_energy, gcol, 256, 0, a, st)) != HG_OK) return s;
+        if ((s = launch(p, K_ROW_MP_INIT, c.rk->mp_init[1], grow, c.rk->nt, c.rk->smem, a0, st)) != HG_OK) return s;
+        for (int it = 0; it < n_iter; ++it) {
+          a.iter = it;
+          if ((s = launch(p, K_COL_GS, c.ck->gs[1], gcol, c.ck->nt, c.ck->smem, a, st)) != HG_OK) return s;
+          const bool last = it == n_iter - 1;
+          if ((s = launch(p, K_ROW_MP, c.rk->mp[last], grow, c.rk->nt, c.rk->smem, last ? ao : a, st)) != HG_OK)
+            return s;
+        }
+        a.iter = n_iter;
+        if ((s = launch(p, K_COL_NMSE, c.ck->gs[0], gcol, c.ck->nt, c.ck->smem, a, st)) != HG_OK) return s;
+        continue;
       }
       const dim3 grow(c.row_blocks(), nb), gcol(c.col_blocks(), nb);
       // prologue (writes h_0 out when there is no iteration)
@@ -664,6 +740,103 @@ hg_status hg_ospr_run(hg_plan* p, const float* const* target_amp, int32_t n_subf
     }
   }
   return HG_OK;
+}
+
+// Shared driver of the gradient-descent calls.  FWD: forward row pass (h = e^{i phi}, per-plane row
+// FFTs -> checkpoint fields) and forward column pass (loss statistics, loss_out).  BWD: backward
+// column pass (adjoint fields) and backward row pass (gradient; Adam when adam).
+static hg_status gd_run(hg_plan* p, float* const* phase, const float* const* target_int, float* const* adam_m,
+                        float* const* adam_v, bool adam, int32_t step, float lr, float beta1, float beta2, float eps,
+                        float* loss_out, float* const* grad_out, const float* grad_scale, bool fwd, bool bwd,
+                        void* stream) {
+  if (!p) return fail(HG_ERR_INVALID_ARG, "plan is NULL");
+  if (!phase || !target_int) return fail(HG_ERR_INVALID_ARG, "phase / target_int is NULL");
+  if (p->levels != 0) return fail(HG_ERR_INVALID_ARG, "gradient descent needs a continuous-phase plan");
+  if (adam) {
+    if (!adam_m || !adam_v) return fail(HG_ERR_INVALID_ARG, "adam_m / adam_v is NULL");
+    if (step < 1) return fail(HG_ERR_INVALID_ARG, "step must be >= 1");
+    if (!(lr > 0.f) || !(beta1 >= 0.f && beta1 < 1.f) || !(beta2 >= 0.f && beta2 < 1.f) || !(eps > 0.f))
+      return fail(HG_ERR_INVALID_ARG, "Adam needs lr > 0, 0 <= beta < 1, eps > 0");
+  }
+  DeviceGuard g(p->device);
+  if (!g.ok) return fail(HG_ERR_CUDA, "cannot select device %d", p->device);
+  hg_status s;
+  const int P = p->P;
+  for (int i = 0; i < p->n_items; ++i) {
+    const size_t px = (size_t)p->H[i] * p->W[i];
+    if ((s = check_ptr(p, phase[i], px * 4, 4, "phase", i)) != HG_OK) return s;
+    for (int q = 0; q < P; ++q)
+      if ((s = check_ptr(p, target_int[i * P + q], px * 4, 4, "target_int", i * P + q)) != HG_OK) return s;
+    if (adam && ((s = check_ptr(p, adam_m[i], px * 4, 4, "adam_m", i)) != HG_OK ||
+                 (s = check_ptr(p, adam_v[i], px * 4, 4, "adam_v", i)) != HG_OK))
+      return s;
+    if (grad_out && grad_out[i] && (s = check_ptr(p, grad_out[i], px * 4, 4, "grad_out", i)) != HG_OK) return s;
+  }
+  if (loss_out && (s = check_ptr(p, loss_out, (size_t)p->n_items * (P + 1) * 4, 4, "loss_out", 0)) != HG_OK) return s;
+  if (grad_scale && (s = check_ptr(p, grad_scale, 4, 4, "grad_scale", 0)) != HG_OK) return s;
+
+  cudaStream_t st = (cudaStream_t)stream;
+  const int chunk = chunk_items(p);
+  for (const SizeClass& c : p->classes) {
+    for (size_t c0 = 0; c0 < c.items.size(); c0 += chunk) {
+      const int nb = (int)std::min<size_t>(chunk, c.items.size() - c0);
+      hg::PassArgs a{};
+      fill_common(p, c, 0, a);
+      a.n_levels = 0;
+      a.n_items = nb;
+      a.loss = loss_out;
+      a.grad_scale = grad_scale;
+      a.adam = adam ? 1 : 0;
+      if (adam) {
+        a.lr = lr;
+        a.beta1 = beta1;
+        a.beta2 = beta2;
+        a.eps = eps;
+        a.bc1 = (float)(1.0 - std::pow((double)beta1, (double)step));
+        a.bc2 = (float)(1.0 - std::pow((double)beta2, (double)step));
+      }
+      for (int k = 0; k < nb; ++k) {
+        const int item = c.items[c0 + k];
+        a.item_index[k] = item;
+        a.class_slot[k] = (int)(c0 + k);
+        for (int q = 0; q < P; ++q) a.target[k * P + q] = target_int[item * P + q];
+        a.phi[k] = phase[item];
+        a.adam_m[k] = adam ? adam_m[item] : nullptr;
+        a.adam_v[k] = adam ? adam_v[item] : nullptr;
+        a.grad[k] = grad_out ? grad_out[item] : nullptr;
+      }
+      const dim3 grow(c.row_blocks(), nb), gcol(c.col_blocks(), nb * P);
+      if (fwd) {
+        if ((s = launch(p, K_ROW_GD_FWD, c.rk->mp_init[0], grow, c.rk->nt, c.rk->smem, a, st)) != HG_OK) return s;
+        if ((s = launch(p, K_COL_GD_FWD, c.ck->gd[0], gcol, c.ck->nt, c.ck->smem, a, st)) != HG_OK) return s;
+      }
+      if (bwd) {
+        if ((s = launch(p, K_COL_GD_BWD, c.ck->gd[1], gcol, c.ck->nt, c.ck->smem, a, st)) != HG_OK) return s;
+        if ((s = launch(p, K_ROW_GD_BWD, c.rk->gd_bwd, grow, c.rk->nt, c.rk->smem, a, st)) != HG_OK) return s;
+      }
+    }
+  }
+  return HG_OK;
+}
+
+hg_status hg_gd_step(hg_plan* p, float* const* phase, const float* const* target_int, float* const* adam_m,
+                     float* const* adam_v, int32_t step, float lr, float beta1, float beta2, float eps, float* loss_out,
+                     float* const* grad_out, void* stream) {
+  return gd_run(p, phase, target_int, adam_m, adam_v, true, step, lr, beta1, beta2, eps, loss_out, grad_out,
+                nullptr, true, true, stream);
+}
+
+hg_status hg_gd_forward(hg_plan* p, float* const* phase, const float* const* target_int, float* loss_out,
+                        void* stream) {
+  return gd_run(p, phase, target_int, nullptr, nullptr, false, 0, 0.f, 0.f, 0.f, 0.f, loss_out, nullptr, nullptr,
+                true, false, stream);
+}
+
+hg_status hg_gd_backward(hg_plan* p, float* const* phase, const float* const* target_int, const float* grad_scale,
+                         float* const* grad_out, void* stream) {
+  if (!grad_out) return fail(HG_ERR_INVALID_ARG, "grad_out is NULL");
+  return gd_run(p, phase, target_int, nullptr, nullptr, false, 0, 0.f, 0.f, 0.f, 0.f, nullptr, grad_out, grad_scale,
+                false, true, stream);
 }
 
 }  // extern "C"

@@ -19,6 +19,7 @@
 namespace hg {
 
 constexpr int kMaxBatch = 32;  // items per launch (a size class with more items is launched in chunks)
+constexpr int kMaxPlanes = 16;  // replay planes per plan
 
 __host__ __device__ constexpr int hg_max(int a, int b) { return a > b ? a : b; }
 __host__ __device__ constexpr int hg_min(int a, int b) { return a < b ? a : b; }
@@ -85,6 +86,23 @@ struct PassArgs {
   float* acc;                   // class accumulated-intensity buffer: item k at acc + k * H * W
   int acc_read;                 // 1: add to the stored sum, 0: start it
   uint32_t* bits[kMaxBatch];    // [S][H][ceil(W/32)] LSB-first hologram bits, or nullptr
+  // planes (multi-plane GS, gradient descent).  With P planes a launch covers n_items * P <= kMaxBatch
+  // (item, plane) pairs: target[k * P + p]; class buffers are indexed by slot * P + p.
+  int n_planes;                        // P (0 is read as 1)
+  const float2* cxp[kMaxPlanes];       // per-plane chirp factors (Fresnel)
+  const float2* cyp[kMaxPlanes];
+  float* plane_val;                    // class [slot * P + p] per-plane NMSE / loss
+  unsigned* plane_counters;            // class [slot] planes finished
+  double* stats;                       // class [slot * P + p][4]: s, sum T^2, loss, 1/sqrt(sum A^2)
+  // gradient descent
+  float* loss;                         // loss_out [n_items][P + 1] (device) or nullptr
+  float* phi[kMaxBatch];               // phase parameters (in / out)
+  float* adam_m[kMaxBatch];
+  float* adam_v[kMaxBatch];
+  float* grad[kMaxBatch];              // dL/dphi out, or nullptr
+  const float* grad_scale;             // device scalar multiplying the gradient, or nullptr (= 1)
+  int adam;                            // 1: apply the Adam update
+  float lr, beta1, beta2, eps, bc1, bc2;  // Adam; bc1 = 1 - beta1^t, bc2 = 1 - beta2^t
 };
 
 // ---------------------------------------------------------------- pointwise pieces
@@ -148,10 +166,11 @@ __device__ __forceinline__ float phase_0_2pi(float2 h) {
 }
 
 // Block-wide (ab, bb, tt) sums in double, written as this block's partials; the last block to
-// arrive adds all partials in block order (deterministic) and writes
-// NMSE = 1 - ab^2 / (bb tt) to *dst.  No block waits on another.
-__device__ __forceinline__ void nmse_reduce(float ab, float bb, float tt, double* __restrict__ part,
-                                            unsigned* counter, int nblk, float* dst) {
+// arrive adds all partials in block order (deterministic).  Returns true in every thread of that
+// last block; its thread 0 receives the totals in tot[0..2].  The block counter is re-armed for the
+// next launch.  No block waits on another.
+__device__ __forceinline__ bool block_totals(float ab, float bb, float tt, double* __restrict__ part,
+                                             unsigned* counter, int nblk, double* tot) {
   __shared__ double red[3][32];
   __shared__ bool is_last;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nw = (blockDim.x + 31) >> 5;
@@ -188,7 +207,8 @@ __device__ __forceinline__ void nmse_reduce(float ab, float bb, float tt, double
     }
   }
   __syncthreads();
-  if (is_last && warp == 0) {
+  if (!is_last) return false;
+  if (warp == 0) {
     __threadfence();
     a = b = c = 0.0;
     for (int k = lane; k < nblk; k += 32) {
@@ -203,10 +223,47 @@ __device__ __forceinline__ void nmse_reduce(float ab, float bb, float tt, double
       c += __shfl_down_sync(0xffffffffu, c, o);
     }
     if (lane == 0) {
-      double e = 1.0;
-      if (b > 0.0 && c > 0.0) e = 1.0 - (a * a) / (b * c);
-      if (dst) *dst = (float)e;
+      tot[0] = a;
+      tot[1] = b;
+      tot[2] = c;
       *counter = 0u;
+    }
+  }
+  return true;
+}
+
+// NMSE = 1 - (sum I T)^2 / (sum I^2 sum T^2) from block_totals' sums.
+__device__ __forceinline__ double nmse_of(const double* tot) {
+  return (tot[1] > 0.0 && tot[2] > 0.0) ? 1.0 - (tot[0] * tot[0]) / (tot[1] * tot[2]) : 1.0;
+}
+
+// Plane-level step (thread 0 of a plane's last block): stores this plane's value; the last plane
+// of the item to arrive writes the mean over planes (in plane order) to *dst.
+__device__ __forceinline__ void plane_mean(double val, float* vals, unsigned* counter, int P, int p, float* dst) {
+  vals[p] = (float)val;
+  __threadfence();
+  const unsigned prev = atomicAdd(counter, 1u);
+  if (prev == (unsigned)P - 1u) {
+    __threadfence();
+    double m = 0.0;
+    for (int q = 0; q < P; ++q) m += (double)__ldcg(&vals[q]);
+    if (dst) *dst = (float)(m / P);
+    *counter = 0u;
+  }
+}
+
+// NMSE of one (item, plane) column pass: the last block writes it (P = 1) or folds it into the
+// mean over planes.
+__device__ __forceinline__ void nmse_reduce(float ab, float bb, float tt, const PassArgs& a, int slot, int P, int p,
+                                            float* dst) {
+  const int sp = slot * P + p;
+  double tot[3];
+  if (block_totals(ab, bb, tt, a.partials + (size_t)sp * 3 * gridDim.x, a.counters + sp, gridDim.x, tot) &&
+      threadIdx.x == 0) {
+    if (P == 1) {
+      if (dst) *dst = (float)nmse_of(tot);
+    } else {
+      plane_mean(nmse_of(tot), a.plane_val + (size_t)slot * P, a.plane_counters + slot, P, p, dst);
     }
   }
 }
@@ -338,12 +395,16 @@ __global__ void __launch_bounds__(ColCfg<H>::NT) k_col_gs(const __grid_constant_
   using K = ColCfg<H>;
   using G = typename K::G;
   extern __shared__ float2 sm[];
-  const int t = threadIdx.x, k = blockIdx.y;
+  const int P = a.n_planes > 1 ? a.n_planes : 1;
+  const int t = threadIdx.x, k = blockIdx.y / P, p = blockIdx.y % P;
   const int col0 = blockIdx.x * K::C;
   const int W = a.W;
   const int slot = a.class_slot[k];
-  float2* f = a.field + (size_t)slot * H * W;
-  const float* A = a.target[k];
+  float2* f = a.field + ((size_t)slot * P + p) * H * W;
+  const float* A = a.target[k * P + p];
+  // with several planes each plane's amplitude is brought to the energy of a unit-modulus field
+  // (A_s = A sqrt(HW / sum A^2)); the common sqrt(HW) is dropped.  One plane needs no scale.
+  const float amp_scale = P > 1 ? (float)__ldcg(&a.stats[((size_t)slot * P + p) * 4 + 3]) : 1.f;
   float2 v[K::V];
   for_each_slot<G, K::RB>(t, [&](int s, int b, int n) {
     const int col = col0 + b;
@@ -360,7 +421,10 @@ __global__ void __launch_bounds__(ColCfg<H>::NT) k_col_gs(const __grid_constant_
     s_it = fmaf(i2, tt, s_it);
     s_ii = fmaf(i2, i2, s_ii);
     s_tt = fmaf(tt, tt, s_tt);
-    if (REPLACE) v[s] = i2 > 0.f ? c_scale(r, amp * rsqrtf(i2)) : make_float2(amp, 0.f);
+    if (REPLACE) {
+      const float as = amp * amp_scale;
+      v[s] = i2 > 0.f ? c_scale(r, as * rsqrtf(i2)) : make_float2(as, 0.f);
+    }
   });
   if (REPLACE) {
     FftRun<G, true, 1, typename K::Inv>::run(v, sm, t, a.tw_col);
@@ -370,7 +434,7 @@ __global__ void __launch_bounds__(ColCfg<H>::NT) k_col_gs(const __grid_constant_
     });
   }
   float* dst = a.nmse ? a.nmse + (size_t)a.item_index[k] * a.nmse_stride + a.iter : nullptr;
-  nmse_reduce(s_it, s_ii, s_tt, a.partials + (size_t)slot * 3 * gridDim.x, a.counters + slot, gridDim.x, dst);
+  nmse_reduce(s_it, s_ii, s_tt, a, slot, P, p, dst);
 }
 
 // Bare column FFTs (propagation), in place on out: FFT -> (times conj chirp when POST) -> scale.
@@ -478,7 +542,7 @@ __global__ void __launch_bounds__(ColCfg<H>::NT) k_col_ospr(const __grid_constan
   }
   if (FINISH) {
     float* dst = a.nmse ? a.nmse + (size_t)a.item_index[k] * a.nmse_stride + (a.iter - 1) : nullptr;
-    nmse_reduce(s_it, s_ii, s_tt, a.partials + (size_t)slot * 3 * gridDim.x, a.counters + slot, gridDim.x, dst);
+    nmse_reduce(s_it, s_ii, s_tt, a, slot, 1, 0, dst);
   }
 }
 
@@ -537,6 +601,260 @@ __global__ void __launch_bounds__(RowCfg<W>::NT) k_row_ospr(const __grid_constan
   for_each_slot<G, K::RE>(t, [&](int s, int b, int n) {
     const int row = row0 + b;
     if (row < H) f[(size_t)row * W + n] = v[s];
+  });
+}
+
+// ---------------------------------------------------------------- planes: multi-plane GS and GD
+//
+// Multi-plane GS (averaged projections):
+//   h <- P_SLM( sum_p conj(c_p) F^-1( A_p R_p / |R_p| ) ),  R_p = F(h c_p)
+// is alternating projection in the product space of the P replay fields.  Gradient descent
+// (Wirtinger) on phase phi with the optimal-scale intensity loss
+//   L = (1/P) sum_p sum (s_p I_p - T_p)^2 / sum T_p^2,  I_p = |F(e^{i phi} c_p)|^2
+// has dL/dphi = 2 Im(g conj(h)), g = sum_p conj(c_p) F^-1((2/P) s_p (s_p I_p - T_p)/sum T_p^2 U_p).
+// With unnormalised transforms (U_u = sqrt(HW) U, s_u = s / HW) the same g is
+// sum_p conj(c_p) F_u^-1((2/P) s_u (s_u I_u - T_p)/sum T_p^2 U_u): the HW factors cancel.
+
+__device__ __forceinline__ float2 chirp_at(const PassArgs& a, int p, int n, int row) {
+  return c_mul(__ldg(&a.cxp[p][n]), __ldg(&a.cyp[p][row]));
+}
+
+// Start of a multi-plane run: h = P_SLM(exp(i phi)) (PROJECT; else h = exp(i phi) exactly, for
+// gradient descent), then for every plane p: forward row FFTs of h c_p -> field p.
+// GD reads phi from a.phi[k]; GS from a.phase_in[k] or the seed.
+template <int W, bool PROJECT>
+__global__ void __launch_bounds__(RowCfg<W>::NT) k_row_mp_init(const __grid_constant__ PassArgs a) {
+  using K = RowCfg<W>;
+  using G = typename K::G;
+  constexpr int R0 = RFirst<typename K::Fwd>::value;
+  extern __shared__ float2 sm[];
+  const int P = a.n_planes > 1 ? a.n_planes : 1;
+  const int t = threadIdx.x, k = blockIdx.y;
+  const int row0 = blockIdx.x * K::ROWS;
+  const int H = a.H;
+  const int slot = a.class_slot[k];
+  const float* ph = PROJECT ? a.phase_in[k] : a.phi[k];
+  float* po = PROJECT ? a.phase_out[k] : nullptr;
+  uint8_t* lo = PROJECT ? a.level_out[k] : nullptr;
+  float2 h0[K::V];
+  for_each_slot<G, R0>(t, [&](int s, int b, int n) {
+    const int row = row0 + b;
+    float2 h = make_float2(0.f, 0.f);
+    if (row < H) {
+      const size_t px = (size_t)row * W + n;
+      float2 e;
+      if (ph) {
+        float sn, cs;
+        sincosf(__ldg(&ph[px]), &sn, &cs);
+        e = make_float2(cs, sn);
+      } else {
+        e = init_unit((uint32_t)px, a.seed, a.item_index[k]);
+      }
+      h = e;
+      if (PROJECT) {
+        int q;
+        h = slm_project(e, a.n_levels, a.lev, q);
+        if (po) po[px] = a.n_levels ? __ldg(&a.lev_phase[q]) : phase_0_2pi(h);
+        if (lo) lo[px] = (uint8_t)q;
+      }
+    }
+    h0[s] = h;
+  });
+  for (int p = 0; p < P; ++p) {
+    float2 v[K::V];
+    for_each_slot<G, R0>(t, [&](int s, int b, int n) {
+      const int row = row0 + b;
+      v[s] = (a.cxp[p] && row < H) ? c_mul(h0[s], chirp_at(a, p, n, row)) : h0[s];
+    });
+    FftRun<G, false, 1, typename K::Fwd>::run(v, sm, t, a.tw_row);
+    float2* f = a.field + ((size_t)slot * P + p) * H * W;
+    for_each_slot<G, RLast<typename K::Fwd>::value>(t, [&](int s, int b, int n) {
+      const int row = row0 + b;
+      if (row < H) f[(size_t)row * W + n] = v[s];
+    });
+  }
+}
+
+// Multi-plane GS row pass: for every plane inverse row FFTs and conj chirp, summed; SLM projection
+// of the sum (optionally written out); for every plane chirp and forward row FFTs.
+template <int W, bool OUT>
+__global__ void __launch_bounds__(RowCfg<W>::NT) k_row_mp(const __grid_constant__ PassArgs a) {
+  using K = RowCfg<W>;
+  using G = typename K::G;
+  extern __shared__ float2 sm[];
+  const int P = a.n_planes > 1 ? a.n_planes : 1;
+  const int t = threadIdx.x, k = blockIdx.y;
+  const int row0 = blockIdx.x * K::ROWS;
+  const int H = a.H;
+  const int slot = a.class_slot[k];
+  float2 g[K::V];
+#pragma unroll
+  for (int i = 0; i < K::V; ++i) g[i] = make_float2(0.f, 0.f);
+  for (int p = 0; p < P; ++p) {
+    const float2* f = a.field + ((size_t)slot * P + p) * H * W;
+    float2 v[K::V];
+    for_each_slot<G, K::RE>(t, [&](int s, int b, int n) {
+      const int row = row0 + b;
+      v[s] = row < H ? f[(size_t)row * W + n] : make_float2(0.f, 0.f);
+    });
+    FftRun<G, true, 1, typename K::Inv>::run(v, sm, t, a.tw_row);
+    for_each_slot<G, K::RM>(t, [&](int s, int b, int n) {
+      const int row = row0 + b;
+      const float2 x = (a.cxp[p] && row < H) ? c_mulc(v[s], chirp_at(a, p, n, row)) : v[s];
+      g[s] = c_add(g[s], x);
+    });
+  }
+  float* po = OUT ? a.phase_out[k] : nullptr;
+  uint8_t* lo = OUT ? a.level_out[k] : nullptr;
+  for_each_slot<G, K::RM>(t, [&](int s, int b, int n) {
+    const int row = row0 + b;
+    int q;
+    const float2 h = slm_project(g[s], a.n_levels, a.lev, q);
+    if (OUT && row < H) {
+      const size_t px = (size_t)row * W + n;
+      if (po) po[px] = a.n_levels ? __ldg(&a.lev_phase[q]) : phase_0_2pi(h);
+      if (lo) lo[px] = (uint8_t)q;
+    }
+    g[s] = row < H ? h : make_float2(0.f, 0.f);
+  });
+  for (int p = 0; p < P; ++p) {
+    float2 v[K::V];
+    for_each_slot<G, K::RM>(t, [&](int s, int b, int n) {
+      const int row = row0 + b;
+      v[s] = (a.cxp[p] && row < H) ? c_mul(g[s], chirp_at(a, p, n, row)) : g[s];
+    });
+    FftRun<G, false, 1, typename K::Fwd>::run(v, sm, t, a.tw_row);
+    float2* f = a.field + ((size_t)slot * P + p) * H * W;
+    for_each_slot<G, K::RE>(t, [&](int s, int b, int n) {
+      const int row = row0 + b;
+      if (row < H) f[(size_t)row * W + n] = v[s];
+    });
+  }
+}
+
+// Gradient-descent column pass, one (item, plane) per blockIdx.y.  Forward (BWD = false): the loss
+// statistics sum I T, sum I^2, sum T^2 of U = F(h c_p) (I = |U|^2, T the target intensity); the last
+// block stores s_u, sum T^2 and the plane loss, and the last plane the mean loss.  Backward: the
+// adjoint field (2/P) s_u (s_u I - T) / sum T^2 U, inverse column FFTs -> field p (in place).
+template <int H, bool BWD>
+__global__ void __launch_bounds__(ColCfg<H>::NT) k_col_gd(const __grid_constant__ PassArgs a) {
+  using K = ColCfg<H>;
+  using G = typename K::G;
+  extern __shared__ float2 sm[];
+  const int P = a.n_planes > 1 ? a.n_planes : 1;
+  const int t = threadIdx.x, k = blockIdx.y / P, p = blockIdx.y % P;
+  const int col0 = blockIdx.x * K::C;
+  const int W = a.W;
+  const int slot = a.class_slot[k];
+  const int sp = slot * P + p;
+  float2* f = a.field + (size_t)sp * H * W;
+  const float* T = a.target[k * P + p];
+  float2 v[K::V];
+  for_each_slot<G, K::RB>(t, [&](int s, int b, int n) {
+    const int col = col0 + b;
+    v[s] = col < W ? f[(size_t)n * W + col] : make_float2(0.f, 0.f);
+  });
+  FftRun<G, false, 1, typename K::Fwd>::run(v, sm, t, a.tw_col);
+  if (!BWD) {
+    float s_it = 0.f, s_ii = 0.f, s_tt = 0.f;
+    for_each_slot<G, RLast<typename K::Fwd>::value>(t, [&](int s, int b, int n) {
+      const int col = col0 + b;
+      if (col < W) {
+        const float2 u = v[s];
+        const float i2 = fmaf(u.x, u.x, u.y * u.y);
+        const float tt = __ldg(&T[(size_t)n * W + col]);
+        s_it = fmaf(i2, tt, s_it);
+        s_ii = fmaf(i2, i2, s_ii);
+        s_tt = fmaf(tt, tt, s_tt);
+      }
+    });
+    double tot[3];
+    if (block_totals(s_it, s_ii, s_tt, a.partials + (size_t)sp * 3 * gridDim.x, a.counters + sp, gridDim.x, tot) &&
+        t == 0) {
+      const double loss = nmse_of(tot);
+      double* st = a.stats + (size_t)sp * 4;
+      st[0] = tot[1] > 0.0 ? tot[0] / tot[1] : 0.0;
+      st[1] = tot[2];
+      st[2] = loss;
+      float* lrow = a.loss ? a.loss + (size_t)a.item_index[k] * (P + 1) : nullptr;
+      if (lrow) lrow[p] = (float)loss;
+      plane_mean(loss, a.plane_val + (size_t)slot * P, a.plane_counters + slot, P, p, lrow ? lrow + P : nullptr);
+    }
+  } else {
+    const double* st = a.stats + (size_t)sp * 4;
+    const float su = (float)__ldcg(&st[0]);
+    const float coef = (float)(2.0 / P * __ldcg(&st[0]) / (__ldcg(&st[1]) > 0.0 ? __ldcg(&st[1]) : 1.0));
+    for_each_slot<G, RLast<typename K::Fwd>::value>(t, [&](int s, int b, int n) {
+      const int col = col0 + b;
+      float2 gi = make_float2(0.f, 0.f);
+      if (col < W) {
+        const float2 u = v[s];
+        const float i2 = fmaf(u.x, u.x, u.y * u.y);
+        const float tt = __ldg(&T[(size_t)n * W + col]);
+        gi = c_scale(u, coef * fmaf(su, i2, -tt));
+      }
+      v[s] = gi;
+    });
+    FftRun<G, true, 1, typename K::Inv>::run(v, sm, t, a.tw_col);
+    for_each_slot<G, K::RB>(t, [&](int s, int b, int n) {
+      const int col = col0 + b;
+      if (col < W) f[(size_t)n * W + col] = v[s];
+    });
+  }
+}
+
+// Gradient-descent backward row pass: g = sum_p conj(c_p) (inverse row FFTs of field p);
+// dL/dphi = 2 Im(g conj(e^{i phi})) (times *grad_scale); optional gradient out and Adam update of
+// phi, m, v in place.
+template <int W>
+__global__ void __launch_bounds__(RowCfg<W>::NT) k_row_gd_bwd(const __grid_constant__ PassArgs a) {
+  using K = RowCfg<W>;
+  using G = typename K::G;
+  extern __shared__ float2 sm[];
+  const int P = a.n_planes > 1 ? a.n_planes : 1;
+  const int t = threadIdx.x, k = blockIdx.y;
+  const int row0 = blockIdx.x * K::ROWS;
+  const int H = a.H;
+  const int slot = a.class_slot[k];
+  float2 g[K::V];
+#pragma unroll
+  for (int i = 0; i < K::V; ++i) g[i] = make_float2(0.f, 0.f);
+  for (int p = 0; p < P; ++p) {
+    const float2* f = a.field + ((size_t)slot * P + p) * H * W;
+    float2 v[K::V];
+    for_each_slot<G, K::RE>(t, [&](int s, int b, int n) {
+      const int row = row0 + b;
+      v[s] = row < H ? f[(size_t)row * W + n] : make_float2(0.f, 0.f);
+    });
+    FftRun<G, true, 1, typename K::Inv>::run(v, sm, t, a.tw_row);
+    for_each_slot<G, K::RM>(t, [&](int s, int b, int n) {
+      const int row = row0 + b;
+      const float2 x = (a.cxp[p] && row < H) ? c_mulc(v[s], chirp_at(a, p, n, row)) : v[s];
+      g[s] = c_add(g[s], x);
+    });
+  }
+  const float gs = a.grad_scale ? __ldg(a.grad_scale) : 1.f;
+  float* phi = a.phi[k];
+  float* gout = a.grad[k];
+  float* m = a.adam_m[k];
+  float* vv = a.adam_v[k];
+  for_each_slot<G, K::RM>(t, [&](int s, int b, int n) {
+    const int row = row0 + b;
+    if (row >= H) return;
+    const size_t px = (size_t)row * W + n;
+    const float ph = phi[px];
+    float sn, cs;
+    sincosf(ph, &sn, &cs);
+    // Im(g conj(h)) with h = (cs, sn)
+    const float gr = 2.f * gs * fmaf(g[s].y, cs, -g[s].x * sn);
+    if (gout) gout[px] = gr;
+    if (a.adam) {
+      const float m1 = fmaf(a.beta1, m[px], (1.f - a.beta1) * gr);
+      const float v1 = fmaf(a.beta2, vv[px], (1.f - a.beta2) * gr * gr);
+      m[px] = m1;
+      vv[px] = v1;
+      phi[px] = ph - a.lr * (m1 / a.bc1) / (sqrtf(v1 / a.bc2) + a.eps);
+    }
   });
 }
 

@@ -15,6 +15,9 @@ struct RowKernels {
   const void* fft[2][2];    // k_row_fft<INV><PRE>
   const void* ospr[2];      // k_row_ospr<BITS = false / true>
   int smem_ospr;            // dynamic shared memory of k_row_ospr (field tile + bit decisions)
+  const void* mp_init[2];   // k_row_mp_init<PROJECT = false (gradient descent) / true (GS)>
+  const void* mp[2];        // k_row_mp<OUT = false / true>
+  const void* gd_bwd;       // k_row_gd_bwd
   void (*set_attrs)();      // raises the dynamic shared-memory limit on the current device
 };
 
@@ -25,6 +28,7 @@ struct ColKernels {
   const void* gs[2];        // k_col_gs<REPLACE = false / true>
   const void* fft[2][2];    // k_col_fft<INV><POST>
   const void* ospr[3];      // k_col_ospr: [0] start only, [1] finish + start, [2] finish only
+  const void* gd[2];        // k_col_gd<BWD = false / true>
   void (*set_attrs)();
 };
 

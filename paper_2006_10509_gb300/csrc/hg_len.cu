@@ -32,6 +32,11 @@ RowKernels make_row() {
   r.ospr[0] = (const void*)&k_row_ospr<N, false>;
   r.ospr[1] = (const void*)&k_row_ospr<N, true>;
   r.smem_ospr = K::SMEM + K::ROWS * N;
+  r.mp_init[0] = (const void*)&k_row_mp_init<N, false>;
+  r.mp_init[1] = (const void*)&k_row_mp_init<N, true>;
+  r.mp[0] = (const void*)&k_row_mp<N, false>;
+  r.mp[1] = (const void*)&k_row_mp<N, true>;
+  r.gd_bwd = (const void*)&k_row_gd_bwd<N>;
   return r;
 }
 
@@ -51,6 +56,8 @@ ColKernels make_col() {
   c.ospr[0] = (const void*)&k_col_ospr<N, false, true>;
   c.ospr[1] = (const void*)&k_col_ospr<N, true, true>;
   c.ospr[2] = (const void*)&k_col_ospr<N, true, false>;
+  c.gd[0] = (const void*)&k_col_gd<N, false>;
+  c.gd[1] = (const void*)&k_col_gd<N, true>;
   return c;
 }
 
@@ -64,6 +71,11 @@ void set_row_attrs(const RowKernels& r) {
   allow_smem(&k_row_fft<HG_LEN, true, true>, r.smem);
   allow_smem(&k_row_ospr<HG_LEN, false>, r.smem_ospr);
   allow_smem(&k_row_ospr<HG_LEN, true>, r.smem_ospr);
+  allow_smem(&k_row_mp_init<HG_LEN, false>, r.smem);
+  allow_smem(&k_row_mp_init<HG_LEN, true>, r.smem);
+  allow_smem(&k_row_mp<HG_LEN, false>, r.smem);
+  allow_smem(&k_row_mp<HG_LEN, true>, r.smem);
+  allow_smem(&k_row_gd_bwd<HG_LEN>, r.smem);
 }
 
 void set_col_attrs(const ColKernels& c) {
@@ -76,6 +88,8 @@ void set_col_attrs(const ColKernels& c) {
   allow_smem(&k_col_ospr<HG_LEN, false, true>, c.smem);
   allow_smem(&k_col_ospr<HG_LEN, true, true>, c.smem);
   allow_smem(&k_col_ospr<HG_LEN, true, false>, c.smem);
+  allow_smem(&k_col_gd<HG_LEN, false>, c.smem);
+  allow_smem(&k_col_gd<HG_LEN, true>, c.smem);
 }
 
 }  // namespace
