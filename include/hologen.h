@@ -186,7 +186,7 @@ HG_API hg_status hg_gd_backward(hg_plan* plan, float* const* phase, const float*
  * Same algorithm, kernels and argument meanings as hg_gs_run with a one-item, one-plane Fourier plan
  * (quant_levels as in hg_plan_desc; target_amp, init_phase, phase_out, level_out are single device
  * pointers; nmse_out is [n_iter + 1]).  Its scratch (field, reduction partials and counter, twiddle
- * and level tables) is a static device array of 8 MiB + 91 KiB that every device which loads this
+ * and level tables) is a static device array of 8 MiB + 155 KiB that every device which loads this
  * library keeps until the process exits.
  *  - Limits: height * width <= 1048576 pixels, each a supported FFT length; larger sizes return
  *    HG_ERR_UNSUPPORTED_SIZE before anything is launched.

@@ -258,13 +258,17 @@ hg_status launch(hg_plan* p, int kind, const void* fn, dim3 grid, int nt, int sm
   return HG_OK;
 }
 
-// twiddles exp(-2 pi i t / n), t < n, in float64 then rounded
-std::vector<float2> twiddles(int n) {
-  std::vector<float2> t(n);
+// per-stage twiddle tables: entry off + (r-1) ns + k = exp(-2 pi i r k / (ns R)), float64 then rounded
+std::vector<float2> twiddles(const hg::TwiddleLayout& l) {
+  std::vector<float2> t(l.size > 0 ? l.size : 1, make_float2(1.f, 0.f));
   const double two_pi = 6.283185307179586476925286766559;
-  for (int i = 0; i < n; ++i) {
-    const double a = two_pi * (double)i / (double)n;
-    t[i] = make_float2((float)std::cos(a), (float)-std::sin(a));
+  for (int i = 0; i < l.count; ++i) {
+    const int ns = l.ns[i], r = l.r[i], n = ns * r;
+    for (int q = 1; q < r; ++q)
+      for (int k = 0; k < ns; ++k) {
+        const double a = two_pi * (double)((q * k) % n) / (double)n;
+        t[l.off[i] + (q - 1) * ns + k] = make_float2((float)std::cos(a), (float)-std::sin(a));
+      }
   }
   return t;
 }
@@ -492,7 +496,7 @@ hg_status hg_plan_create(const hg_plan_desc* d, hg_plan** out) {
     for (int len : {c.H, c.W}) {
       if (p->tw.count(len)) continue;
       float2* t = nullptr;
-      if ((s = upload(p, &t, twiddles(len), "twiddle table")) != HG_OK) return bail(s);
+      if ((s = upload(p, &t, twiddles(hg::row_kernels(len)->tw), "twiddle table")) != HG_OK) return bail(s);
       p->tw[len] = t;
     }
   }
@@ -639,13 +643,13 @@ hg_status hg_gs_run(hg_plan* p, const float* const* target_amp, const float* con
         if ((s = launch(p, K_ROW_MP_INIT, c.rk->mp_init[1], grow, c.rk->nt, c.rk->smem, a0, st)) != HG_OK) return s;
         for (int it = 0; it < n_iter; ++it) {
           a.iter = it;
-          if ((s = launch(p, K_COL_GS, c.ck->gs[1], gcol, c.ck->nt, c.ck->smem, a, st)) != HG_OK) return s;
+          if ((s = launch(p, K_COL_GS, c.ck->gs[1], gcol, c.ck->nt, c.ck->smem_gs, a, st)) != HG_OK) return s;
           const bool last = it == n_iter - 1;
           if ((s = launch(p, K_ROW_MP, c.rk->mp[last], grow, c.rk->nt, c.rk->smem, last ? ao : a, st)) != HG_OK)
             return s;
         }
         a.iter = n_iter;
-        if ((s = launch(p, K_COL_NMSE, c.ck->gs[0], gcol, c.ck->nt, c.ck->smem, a, st)) != HG_OK) return s;
+        if ((s = launch(p, K_COL_NMSE, c.ck->gs[0], gcol, c.ck->nt, c.ck->smem_gs, a, st)) != HG_OK) return s;
         continue;
       }
       const dim3 grow(c.row_blocks(), nb), gcol(c.col_blocks(), nb);
@@ -666,12 +670,12 @@ hg_status hg_gs_run(hg_plan* p, const float* const* target_amp, const float* con
       }
       for (int it = 0; it < n_iter; ++it) {
         a.iter = it;
-        if ((s = launch(p, K_COL_GS, c.ck->gs[1], gcol, c.ck->nt, c.ck->smem, a, st)) != HG_OK) return s;
+        if ((s = launch(p, K_COL_GS, c.ck->gs[1], gcol, c.ck->nt, c.ck->smem_gs, a, st)) != HG_OK) return s;
         const bool last = it == n_iter - 1;
         if ((s = launch(p, K_ROW_GS, c.rk->gs[last], grow, c.rk->nt, c.rk->smem, last ? ao : a, st)) != HG_OK) return s;
       }
       a.iter = n_iter;
-      if ((s = launch(p, K_COL_NMSE, c.ck->gs[0], gcol, c.ck->nt, c.ck->smem, a, st)) != HG_OK) return s;
+      if ((s = launch(p, K_COL_NMSE, c.ck->gs[0], gcol, c.ck->nt, c.ck->smem_gs, a, st)) != HG_OK) return s;
     }
   }
   return HG_OK;
@@ -728,7 +732,7 @@ hg_status hg_ospr_run(hg_plan* p, const float* const* target_amp, int32_t n_subf
         a.iter = sf;
         if ((s = launch(p, K_ROW_OSPR, c.rk->ospr[n_iter == 0], grow, c.rk->nt, rs, a, st)) != HG_OK) return s;
         for (int it = 0; it < n_iter; ++it) {
-          if ((s = launch(p, K_COL_GS, c.ck->gs[1], gcol, c.ck->nt, c.ck->smem, ag, st)) != HG_OK) return s;
+          if ((s = launch(p, K_COL_GS, c.ck->gs[1], gcol, c.ck->nt, c.ck->smem_gs, ag, st)) != HG_OK) return s;
           if ((s = launch(p, K_ROW_OSPR, c.rk->ospr[it == n_iter - 1], grow, c.rk->nt, rs, a, st)) != HG_OK)
             return s;
         }

@@ -236,6 +236,17 @@ struct RProd<RList<R, Rs...>> {
   static constexpr int value = R * RProd<RList<Rs...>>::value;
 };
 
+template <class L>
+struct RArr;
+template <int... Rs>
+struct RArr<RList<Rs...>> {
+  static constexpr int n = sizeof...(Rs);
+  __host__ __device__ static constexpr int at(int s) {
+    const int a[] = {Rs...};
+    return a[s];
+  }
+};
+
 // Radix plan for each supported length (forward order; the inverse of a fused pair runs reversed).
 template <int N>
 struct PlanFor;
@@ -265,6 +276,63 @@ HG_PLAN(1536, 16, 8, 4, 3)
 HG_PLAN(1920, 16, 8, 3, 5)
 #undef HG_PLAN
 
+// Per-stage twiddle tables of length N.  A stage of radix R after Ns earlier points needs
+// w_{Ns R}^{r k} for r = 1..R-1, k = 0..Ns-1; its table stores them r-major, entry (r-1) Ns + k, so a
+// warp whose lanes hold consecutive k reads consecutive entries and the addresses of one butterfly
+// differ by compile-time constants.  The blob holds the tables of every stage (Ns > 1) of the
+// forward plan, then those of the reversed plan that are not already present.
+template <int N>
+struct TwBlob {
+  using F = typename PlanFor<N>::type;
+  using Bk = typename RRev<F>::type;
+  static constexpr int S = RArr<F>::n;
+  __host__ __device__ static constexpr int stage_r(int which, int s) {
+    return which == 0 ? RArr<F>::at(s) : RArr<Bk>::at(s);
+  }
+  __host__ __device__ static constexpr int stage_ns(int which, int s) {
+    int ns = 1;
+    for (int i = 0; i < s; ++i) ns *= stage_r(which, i);
+    return ns;
+  }
+  __host__ __device__ static constexpr bool in_forward(int ns, int r) {
+    for (int s = 1; s < S; ++s)
+      if (stage_ns(0, s) == ns && stage_r(0, s) == r) return true;
+    return false;
+  }
+  // offset of the (ns, r) table, or the blob size when (ns, r) == (0, 0)
+  __host__ __device__ static constexpr int offset(int ns, int r) {
+    int off = 0;
+    for (int which = 0; which < 2; ++which)
+      for (int s = 1; s < S; ++s) {
+        const int ns2 = stage_ns(which, s), r2 = stage_r(which, s);
+        if (which == 1 && in_forward(ns2, r2)) continue;
+        if (ns2 == ns && r2 == r) return off;
+        off += (r2 - 1) * ns2;
+      }
+    return (ns == 0 && r == 0) ? off : -1;
+  }
+  static constexpr int size = offset(0, 0);
+  // number of distinct stage tables and their (ns, r, offset)
+  __host__ __device__ static constexpr int count() {
+    int c = 0;
+    for (int which = 0; which < 2; ++which)
+      for (int s = 1; s < S; ++s)
+        if (!(which == 1 && in_forward(stage_ns(which, s), stage_r(which, s)))) ++c;
+    return c;
+  }
+  __host__ __device__ static constexpr int table(int idx, int field) {
+    int c = 0;
+    for (int which = 0; which < 2; ++which)
+      for (int s = 1; s < S; ++s) {
+        const int ns2 = stage_ns(which, s), r2 = stage_r(which, s);
+        if (which == 1 && in_forward(ns2, r2)) continue;
+        if (c == idx) return field == 0 ? ns2 : (field == 1 ? r2 : offset(ns2, r2));
+        ++c;
+      }
+    return -1;
+  }
+};
+
 // ---------------------------------------------------------------- tile geometry
 
 // B sequences of length N, NT threads.  COLS: a column strip (element (b, n) of the strip at global
@@ -290,7 +358,15 @@ struct Geo {
     return nbf<R>() % NT == 0;
   }
 
-  __device__ __forceinline__ static int sidx(int b, int n) { return COLS ? n * B + b : b * N + n; }
+  // Shared-memory slot of element (b, n), padded by one float2 per 16: the Stockham stores of a stage
+  // with stride R (R = 4, 8, 16) land on distinct banks within each half-warp.
+  __device__ __forceinline__ static int sidx(int b, int n) {
+    const int i = COLS ? n * B + b : b * N + n;
+    return i + (i >> 4);
+  }
+  // float2 slots of the exchange buffer, rounded up to 128 bytes so that data placed after it is
+  // 16-byte aligned (cp.async destinations)
+  static constexpr int SM_ELEMS = (B * N + ((B * N) >> 4) + 15) / 16 * 16;
 
   // butterfly i of thread t in a radix-R stage -> (sequence b, butterfly j); false when past the end
   template <int R>
@@ -342,11 +418,12 @@ __device__ __forceinline__ void stage_compute(float2 (&v)[V], int t, const float
     if (!G::template bf<R>(t, i, b, j)) continue;
     float2* x = &v[i * R];
     if constexpr (NS > 1) {
-      const int k = j % NS;
-      constexpr int step = G::N / (NS * R);
+      constexpr int off = TwBlob<G::N>::offset(NS, R);
+      static_assert(off >= 0, "missing twiddle table");
+      const float2* tp = tw + off + (j % NS);
 #pragma unroll
       for (int r = 1; r < R; ++r) {
-        const float2 w = __ldg(&tw[r * k * step]);
+        const float2 w = __ldg(tp + (r - 1) * NS);
         x[r] = INV ? c_mulc(x[r], w) : c_mul(x[r], w);
       }
     }

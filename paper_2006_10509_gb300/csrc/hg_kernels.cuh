@@ -36,21 +36,61 @@ struct RowCfg {
   static constexpr int RE = RLast<Fwd>::value;   // radix of the global load/store stages
   static constexpr int RM = RFirst<Fwd>::value;  // radix of the pointwise step between the FFTs
   static constexpr int V = MaxV<G, Fwd>::value;
-  static constexpr int SMEM = ROWS * W * 8;
+  static constexpr int SMEM = G::SM_ELEMS * 8;
 };
 
-// Column strip: C columns of length H, about 16 values per thread.
+// Column strip: C columns of length H, about 16 values per thread.  Long columns use 4-column
+// strips (32-byte row segments, one L2 sector) so that two strips share an SM.
 template <int H>
 struct ColCfg {
-  static constexpr int C = H >= 4096 ? 4 : (H >= 640 ? 8 : 16);
+  static constexpr int C = H >= 2048 ? 4 : (H >= 640 ? 8 : 16);
   static constexpr int NT = hg_min(1024, hg_max(32, round_up(C * H / 16, 32)));
   using G = Geo<H, C, NT, true>;
   using Fwd = typename PlanFor<H>::type;
   using Inv = typename RRev<Fwd>::type;
   static constexpr int RB = RFirst<Fwd>::value;  // radix of the global load/store stage
   static constexpr int V = MaxV<G, Fwd>::value;
-  static constexpr int SMEM = C * H * 8;
+  static constexpr int SMEM = G::SM_ELEMS * 8;
+  static constexpr int SMEM_T = SMEM + H * C * 4;  // + the strip's target values (GS passes)
 };
+
+// ---------------------------------------------------------------- asynchronous copies
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Starts copying the strip's target values A[n][col0 .. col0 + C) into ts[n * C + b] (zero past W).
+// 16-byte copies when every row segment is whole and aligned, else 4-byte copies.
+template <int H, int C, int NT>
+__device__ __forceinline__ void prefetch_strip(float* ts, const float* __restrict__ A, int col0, int W) {
+  const int t = threadIdx.x;
+  const bool vec = (C % 4 == 0) && (W % 4 == 0) && (col0 + C <= W) && (((uintptr_t)A & 15) == 0) &&
+                   ((__cvta_generic_to_shared(ts) & 15) == 0);
+  if (vec) {
+    constexpr int CH = C / 4;  // 16-byte chunks per row
+    for (int i = t; i < H * CH; i += NT) {
+      const int n = i / CH, c = i % CH;
+      cp_async16(ts + n * C + 4 * c, A + (size_t)n * W + col0 + 4 * c);
+    }
+  } else {
+    for (int i = t; i < H * C; i += NT) {
+      const int n = i / C, b = i % C;
+      if (col0 + b < W)
+        cp_async4(ts + i, A + (size_t)n * W + col0 + b);
+      else
+        ts[i] = 0.f;
+    }
+  }
+  cp_async_commit();
+}
 
 // ---------------------------------------------------------------- launch arguments
 
@@ -62,8 +102,8 @@ struct PassArgs {
   int n_levels;            // 0 continuous, 2 binary, N >= 3 N-level
   int iter;                // iteration index written by column passes (NMSE slot)
   int nmse_stride;         // floats between items in nmse_out (n_iter + 1)
-  const float2* tw_row;    // twiddles exp(-2 pi i t / W), t < W
-  const float2* tw_col;    // twiddles exp(-2 pi i t / H), t < H
+  const float2* tw_row;    // per-stage twiddle tables of length W (TwBlob<W>)
+  const float2* tw_col;    // per-stage twiddle tables of length H (TwBlob<H>)
   const float2* cx;        // Fresnel chirp along a row (W), nullptr for Fourier
   const float2* cy;        // Fresnel chirp along a column (H)
   const float2* lev;       // level field exp(2 pi i q / N), q < N
@@ -276,7 +316,7 @@ template <int W>
 __global__ void __launch_bounds__(RowCfg<W>::NT) k_row_init(const __grid_constant__ PassArgs a) {
   using K = RowCfg<W>;
   using G = typename K::G;
-  extern __shared__ float2 sm[];
+  extern __shared__ __align__(16) float2 sm[];
   const int t = threadIdx.x, k = blockIdx.y;
   const int row0 = blockIdx.x * K::ROWS;
   const int H = a.H;
@@ -319,7 +359,7 @@ template <int W, bool OUT>
 __global__ void __launch_bounds__(RowCfg<W>::NT) k_row_gs(const __grid_constant__ PassArgs a) {
   using K = RowCfg<W>;
   using G = typename K::G;
-  extern __shared__ float2 sm[];
+  extern __shared__ __align__(16) float2 sm[];
   const int t = threadIdx.x, k = blockIdx.y;
   const int row0 = blockIdx.x * K::ROWS;
   const int H = a.H;
@@ -362,7 +402,7 @@ template <int W, bool INV, bool PRE>
 __global__ void __launch_bounds__(RowCfg<W>::NT) k_row_fft(const __grid_constant__ PassArgs a) {
   using K = RowCfg<W>;
   using G = typename K::G;
-  extern __shared__ float2 sm[];
+  extern __shared__ __align__(16) float2 sm[];
   const int t = threadIdx.x, k = blockIdx.y;
   const int row0 = blockIdx.x * K::ROWS;
   const int H = a.H;
@@ -394,7 +434,7 @@ template <int H, bool REPLACE>
 __global__ void __launch_bounds__(ColCfg<H>::NT) k_col_gs(const __grid_constant__ PassArgs a) {
   using K = ColCfg<H>;
   using G = typename K::G;
-  extern __shared__ float2 sm[];
+  extern __shared__ __align__(16) float2 sm[];
   const int P = a.n_planes > 1 ? a.n_planes : 1;
   const int t = threadIdx.x, k = blockIdx.y / P, p = blockIdx.y % P;
   const int col0 = blockIdx.x * K::C;
@@ -405,17 +445,20 @@ __global__ void __launch_bounds__(ColCfg<H>::NT) k_col_gs(const __grid_constant_
   // with several planes each plane's amplitude is brought to the energy of a unit-modulus field
   // (A_s = A sqrt(HW / sum A^2)); the common sqrt(HW) is dropped.  One plane needs no scale.
   const float amp_scale = P > 1 ? (float)__ldcg(&a.stats[((size_t)slot * P + p) * 4 + 3]) : 1.f;
+  float* ts = reinterpret_cast<float*>(sm + G::SM_ELEMS);  // the strip's target, [n][C]
+  prefetch_strip<H, K::C, K::NT>(ts, A, col0, W);
   float2 v[K::V];
   for_each_slot<G, K::RB>(t, [&](int s, int b, int n) {
     const int col = col0 + b;
     v[s] = col < W ? f[(size_t)n * W + col] : make_float2(0.f, 0.f);
   });
   FftRun<G, false, 1, typename K::Fwd>::run(v, sm, t, a.tw_col);
+  cp_async_wait_all();
+  __syncthreads();
   float s_it = 0.f, s_ii = 0.f, s_tt = 0.f;
   for_each_slot<G, RLast<typename K::Fwd>::value>(t, [&](int s, int b, int n) {
-    const int col = col0 + b;
     const float2 r = v[s];
-    const float amp = col < W ? __ldg(&A[(size_t)n * W + col]) : 0.f;
+    const float amp = ts[n * K::C + b];
     const float i2 = fmaf(r.x, r.x, r.y * r.y);
     const float tt = amp * amp;
     s_it = fmaf(i2, tt, s_it);
@@ -442,7 +485,7 @@ template <int H, bool INV, bool POST>
 __global__ void __launch_bounds__(ColCfg<H>::NT) k_col_fft(const __grid_constant__ PassArgs a) {
   using K = ColCfg<H>;
   using G = typename K::G;
-  extern __shared__ float2 sm[];
+  extern __shared__ __align__(16) float2 sm[];
   const int t = threadIdx.x, k = blockIdx.y;
   const int col0 = blockIdx.x * K::C;
   const int W = a.W;
@@ -490,7 +533,7 @@ template <int H, bool FINISH, bool START>
 __global__ void __launch_bounds__(ColCfg<H>::NT) k_col_ospr(const __grid_constant__ PassArgs a) {
   using K = ColCfg<H>;
   using G = typename K::G;
-  extern __shared__ float2 sm[];
+  extern __shared__ __align__(16) float2 sm[];
   const int t = threadIdx.x, k = blockIdx.y;
   const int col0 = blockIdx.x * K::C;
   const int W = a.W;
@@ -553,8 +596,8 @@ __global__ void __launch_bounds__(RowCfg<W>::NT) k_row_ospr(const __grid_constan
   using K = RowCfg<W>;
   using G = typename K::G;
   constexpr int WORDS = (W + 31) / 32;
-  extern __shared__ float2 sm[];
-  unsigned char* qs = reinterpret_cast<unsigned char*>(sm + K::ROWS * W);  // [ROWS][W] decisions
+  extern __shared__ __align__(16) float2 sm[];
+  unsigned char* qs = reinterpret_cast<unsigned char*>(sm + G::SM_ELEMS);  // [ROWS][W] decisions
   const int t = threadIdx.x, k = blockIdx.y;
   const int row0 = blockIdx.x * K::ROWS;
   const int H = a.H;
@@ -627,7 +670,7 @@ __global__ void __launch_bounds__(RowCfg<W>::NT) k_row_mp_init(const __grid_cons
   using K = RowCfg<W>;
   using G = typename K::G;
   constexpr int R0 = RFirst<typename K::Fwd>::value;
-  extern __shared__ float2 sm[];
+  extern __shared__ __align__(16) float2 sm[];
   const int P = a.n_planes > 1 ? a.n_planes : 1;
   const int t = threadIdx.x, k = blockIdx.y;
   const int row0 = blockIdx.x * K::ROWS;
@@ -681,7 +724,7 @@ template <int W, bool OUT>
 __global__ void __launch_bounds__(RowCfg<W>::NT) k_row_mp(const __grid_constant__ PassArgs a) {
   using K = RowCfg<W>;
   using G = typename K::G;
-  extern __shared__ float2 sm[];
+  extern __shared__ __align__(16) float2 sm[];
   const int P = a.n_planes > 1 ? a.n_planes : 1;
   const int t = threadIdx.x, k = blockIdx.y;
   const int row0 = blockIdx.x * K::ROWS;
@@ -740,7 +783,7 @@ template <int H, bool BWD>
 __global__ void __launch_bounds__(ColCfg<H>::NT) k_col_gd(const __grid_constant__ PassArgs a) {
   using K = ColCfg<H>;
   using G = typename K::G;
-  extern __shared__ float2 sm[];
+  extern __shared__ __align__(16) float2 sm[];
   const int P = a.n_planes > 1 ? a.n_planes : 1;
   const int t = threadIdx.x, k = blockIdx.y / P, p = blockIdx.y % P;
   const int col0 = blockIdx.x * K::C;
@@ -810,7 +853,7 @@ template <int W>
 __global__ void __launch_bounds__(RowCfg<W>::NT) k_row_gd_bwd(const __grid_constant__ PassArgs a) {
   using K = RowCfg<W>;
   using G = typename K::G;
-  extern __shared__ float2 sm[];
+  extern __shared__ __align__(16) float2 sm[];
   const int P = a.n_planes > 1 ? a.n_planes : 1;
   const int t = threadIdx.x, k = blockIdx.y;
   const int row0 = blockIdx.x * K::ROWS;

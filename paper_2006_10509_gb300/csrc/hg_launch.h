@@ -6,6 +6,13 @@
 
 namespace hg {
 
+// Per-stage twiddle tables of one FFT length: table i holds w_{ns R}^{r k} at off + (r-1) ns + k.
+struct TwiddleLayout {
+  int size;       // float2 entries of the blob
+  int count;      // tables
+  int ns[16], r[16], off[16];
+};
+
 struct RowKernels {
   int rows;      // rows per CTA
   int nt;        // threads per CTA
@@ -19,17 +26,20 @@ struct RowKernels {
   const void* mp[2];        // k_row_mp<OUT = false / true>
   const void* gd_bwd;       // k_row_gd_bwd
   void (*set_attrs)();      // raises the dynamic shared-memory limit on the current device
+  TwiddleLayout tw;         // twiddle tables of length W
 };
 
 struct ColKernels {
   int cols;
   int nt;
   int smem;
+  int smem_gs;              // dynamic shared memory of k_col_gs (exchange buffer + target strip)
   const void* gs[2];        // k_col_gs<REPLACE = false / true>
   const void* fft[2][2];    // k_col_fft<INV><POST>
   const void* ospr[3];      // k_col_ospr: [0] start only, [1] finish + start, [2] finish only
   const void* gd[2];        // k_col_gd<BWD = false / true>
   void (*set_attrs)();
+  TwiddleLayout tw;         // twiddle tables of length H
 };
 
 // X-macro of every supported FFT length (rows and columns).

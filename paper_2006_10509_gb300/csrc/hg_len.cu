@@ -16,6 +16,21 @@ void allow_smem(F* f, int bytes) {
 }
 
 template <int N>
+TwiddleLayout make_tw() {
+  using T = TwBlob<N>;
+  static_assert(T::count() <= 16, "too many twiddle tables");
+  TwiddleLayout l{};
+  l.size = T::size;
+  l.count = T::count();
+  for (int i = 0; i < l.count; ++i) {
+    l.ns[i] = T::table(i, 0);
+    l.r[i] = T::table(i, 1);
+    l.off[i] = T::table(i, 2);
+  }
+  return l;
+}
+
+template <int N>
 RowKernels make_row() {
   using K = RowCfg<N>;
   RowKernels r{};
@@ -37,6 +52,7 @@ RowKernels make_row() {
   r.mp[0] = (const void*)&k_row_mp<N, false>;
   r.mp[1] = (const void*)&k_row_mp<N, true>;
   r.gd_bwd = (const void*)&k_row_gd_bwd<N>;
+  r.tw = make_tw<N>();
   return r;
 }
 
@@ -47,6 +63,7 @@ ColKernels make_col() {
   c.cols = K::C;
   c.nt = K::NT;
   c.smem = K::SMEM;
+  c.smem_gs = K::SMEM_T;
   c.gs[0] = (const void*)&k_col_gs<N, false>;
   c.gs[1] = (const void*)&k_col_gs<N, true>;
   c.fft[0][0] = (const void*)&k_col_fft<N, false, false>;
@@ -58,6 +75,7 @@ ColKernels make_col() {
   c.ospr[2] = (const void*)&k_col_ospr<N, true, false>;
   c.gd[0] = (const void*)&k_col_gd<N, false>;
   c.gd[1] = (const void*)&k_col_gd<N, true>;
+  c.tw = make_tw<N>();
   return c;
 }
 
@@ -79,8 +97,8 @@ void set_row_attrs(const RowKernels& r) {
 }
 
 void set_col_attrs(const ColKernels& c) {
-  allow_smem(&k_col_gs<HG_LEN, false>, c.smem);
-  allow_smem(&k_col_gs<HG_LEN, true>, c.smem);
+  allow_smem(&k_col_gs<HG_LEN, false>, c.smem_gs);
+  allow_smem(&k_col_gs<HG_LEN, true>, c.smem_gs);
   allow_smem(&k_col_fft<HG_LEN, false, false>, c.smem);
   allow_smem(&k_col_fft<HG_LEN, false, true>, c.smem);
   allow_smem(&k_col_fft<HG_LEN, true, false>, c.smem);

@@ -21,12 +21,14 @@
 
 namespace {
 
-// Scratch capacity: a field of up to 2^20 pixels (e.g. 1024 x 1024, 2048 x 512) plus tables.
+// Scratch capacity: a field of up to 2^20 pixels (e.g. 1024 x 1024, 2048 x 512) plus tables
+// (8 MiB + 155 KiB).
 constexpr size_t kMaxPixels = size_t(1) << 20;
 constexpr size_t kFieldBytes = kMaxPixels * sizeof(float2);  // 8 MiB
 constexpr size_t kPartialBytes = 3 * 1024 * sizeof(double);  // <= 1024 column strips
 constexpr size_t kCounterBytes = 256;
-constexpr size_t kTwBytes = 4096 * sizeof(float2);           // one twiddle table (length <= 4096)
+constexpr int kTwEntries = 8192;                              // per-stage twiddle tables of one length
+constexpr size_t kTwBytes = kTwEntries * sizeof(float2);
 constexpr size_t kLevBytes = 256 * sizeof(float2);
 constexpr size_t kLevPhaseBytes = 256 * sizeof(float);
 constexpr size_t kOffPartials = kFieldBytes;
@@ -39,23 +41,31 @@ constexpr size_t kScratchBytes = kOffLevPhase + kLevPhaseBytes;
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
-// Fills the twiddle tables exp(-2 pi i t / n) and the level tables for this call's sizes, in
-// float64 then rounded (the values hg_plan_create computes on the host).
-__global__ void k_noalloc_tables(int w, int h, int n_levels) {
+// Entry i of a per-stage twiddle blob: exp(-2 pi i r k / (ns R)) of the table holding i.
+__device__ float2 blob_entry(const hg::TwiddleLayout& l, int i) {
+  for (int t = 0; t < l.count; ++t) {
+    const int ns = l.ns[t], n = ns * l.r[t];
+    if (i >= l.off[t] && i < l.off[t] + (l.r[t] - 1) * ns) {
+      const int q = (i - l.off[t]) / ns + 1, k = (i - l.off[t]) % ns;
+      double s, c;
+      sincospi(2.0 * (double)((q * k) % n) / (double)n, &s, &c);
+      return make_float2((float)c, (float)-s);
+    }
+  }
+  return make_float2(1.f, 0.f);
+}
+
+// Fills the twiddle tables of this call's lengths and the level tables, in float64 then rounded
+// (the values hg_plan_create computes on the host).
+__global__ void k_noalloc_tables(const hg::TwiddleLayout tw_w, const hg::TwiddleLayout tw_h, int n_levels) {
   float2* tw_row = reinterpret_cast<float2*>(g_scratch + kOffTwRow);
   float2* tw_col = reinterpret_cast<float2*>(g_scratch + kOffTwCol);
   float2* lev = reinterpret_cast<float2*>(g_scratch + kOffLev);
   float* lev_phase = reinterpret_cast<float*>(g_scratch + kOffLevPhase);
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   double s, c;
-  if (i < w) {
-    sincospi(2.0 * (double)i / (double)w, &s, &c);
-    tw_row[i] = make_float2((float)c, (float)-s);
-  }
-  if (i < h) {
-    sincospi(2.0 * (double)i / (double)h, &s, &c);
-    tw_col[i] = make_float2((float)c, (float)-s);
-  }
+  if (i < tw_w.size) tw_row[i] = blob_entry(tw_w, i);
+  if (i < tw_h.size) tw_col[i] = blob_entry(tw_h, i);
   const int nl = n_levels > 0 ? n_levels : 1;
   if (i < nl) {
     if ((4 * i) % nl == 0) {
@@ -166,6 +176,7 @@ extern "C" hg_status hg_gs_run_noalloc(int32_t height, int32_t width, int32_t qu
   if (level_out && quant_levels == 0) return err(HG_ERR_INVALID_ARG, "level_out needs quant_levels >= 2");
   if (nmse_out && !is_device_buffer(nmse_out, (size_t)(n_iter + 1) * 4, 4))
     return err(HG_ERR_INVALID_ARG, "nmse_out is not a device buffer of n_iter + 1 floats");
+  if (rk->tw.size > kTwEntries || ck->tw.size > kTwEntries) return err(HG_ERR_INTERNAL, "twiddle tables overflow");
   const int col_blocks = (width + ck->cols - 1) / ck->cols;
   if (col_blocks * 3 * (int)sizeof(double) > (int)kPartialBytes) return err(HG_ERR_INTERNAL, "partials overflow");
 
@@ -181,8 +192,8 @@ extern "C" hg_status hg_gs_run_noalloc(int32_t height, int32_t width, int32_t qu
     cudaGetLastError();
     return err(HG_ERR_CUDA, "counter reset failed");
   }
-  // one thread per table entry: lengths <= 4096, levels <= 256
-  k_noalloc_tables<<<4096 / 256, 256, 0, st>>>(width, height, quant_levels);
+  // one thread per table entry (twiddle blobs <= kTwEntries, levels <= 256)
+  k_noalloc_tables<<<kTwEntries / 256, 256, 0, st>>>(rk->tw, ck->tw, quant_levels);
   if (cudaGetLastError() != cudaSuccess) return err(HG_ERR_CUDA, "table kernel launch failed");
 
   hg::PassArgs a{};
@@ -215,10 +226,10 @@ extern "C" hg_status hg_gs_run_noalloc(int32_t height, int32_t width, int32_t qu
   ao.level_out[0] = level_out;
   for (int it = 0; it < n_iter; ++it) {
     a.iter = it;
-    if ((s = run_kernel(ck->gs[1], gcol, ck->nt, ck->smem, a, st)) != HG_OK) return s;
+    if ((s = run_kernel(ck->gs[1], gcol, ck->nt, ck->smem_gs, a, st)) != HG_OK) return s;
     const bool last = it == n_iter - 1;
     if ((s = run_kernel(rk->gs[last], grow, rk->nt, rk->smem, last ? ao : a, st)) != HG_OK) return s;
   }
   a.iter = n_iter;
-  return run_kernel(ck->gs[0], gcol, ck->nt, ck->smem, a, st);
+  return run_kernel(ck->gs[0], gcol, ck->nt, ck->smem_gs, a, st);
 }
