@@ -14,7 +14,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/hologen.h"
+#include "hologen.h"
 #include "hg_kernels.cuh"
 #include "hg_launch.h"
 

@@ -25,6 +25,21 @@ __host__ __device__ constexpr int hg_max(int a, int b) { return a > b ? a : b; }
 __host__ __device__ constexpr int hg_min(int a, int b) { return a < b ? a : b; }
 __host__ __device__ constexpr int round_up(int a, int m) { return (a + m - 1) / m * m; }
 
+// The value itself, hidden from the optimiser.  Column kernels re-derive their store addresses
+// (which involve the run-time row stride) through it after the second transform, instead of
+// keeping every slot's address live across both transforms.
+__device__ __forceinline__ int opaque(int x) {
+  int y;
+  asm volatile("mov.b32 %0, %1;" : "=r"(y) : "r"(x));
+  return y;
+}
+template <class T>
+__device__ __forceinline__ T* opaque(T* x) {
+  T* y;
+  asm volatile("mov.b64 %0, %1;" : "=l"(y) : "l"(x));
+  return y;
+}
+
 // Row tile: ROWS rows of length W, about 16 values per thread.
 template <int W>
 struct RowCfg {
@@ -52,6 +67,7 @@ struct ColCfg {
   static constexpr int V = MaxV<G, Fwd>::value;
   static constexpr int SMEM = G::SM_ELEMS * 8;
   static constexpr int SMEM_T = SMEM + H * C * 4;  // + the strip's target values (GS passes)
+  static constexpr int MINB = hg_max(1, 1024 / NT);  // CTAs per SM the register budget is cut for
 };
 
 // ---------------------------------------------------------------- asynchronous copies
@@ -431,7 +447,7 @@ __global__ void __launch_bounds__(RowCfg<W>::NT) k_row_fft(const __grid_constant
 // amplitude replacement R' = A R / |R| -> inverse column FFTs.  With REPLACE = false only the NMSE
 // is taken (last iteration) and the field is not written.
 template <int H, bool REPLACE>
-__global__ void __launch_bounds__(ColCfg<H>::NT) k_col_gs(const __grid_constant__ PassArgs a) {
+__global__ void __launch_bounds__(ColCfg<H>::NT, ColCfg<H>::MINB) k_col_gs(const __grid_constant__ PassArgs a) {
   using K = ColCfg<H>;
   using G = typename K::G;
   extern __shared__ __align__(16) float2 sm[];
@@ -450,7 +466,7 @@ __global__ void __launch_bounds__(ColCfg<H>::NT) k_col_gs(const __grid_constant_
   float2 v[K::V];
   for_each_slot<G, K::RB>(t, [&](int s, int b, int n) {
     const int col = col0 + b;
-    v[s] = col < W ? f[(size_t)n * W + col] : make_float2(0.f, 0.f);
+    v[s] = col < W ? f[n * W + col] : make_float2(0.f, 0.f);  // 32-bit offsets: H W < 2^31
   });
   FftRun<G, false, 1, typename K::Fwd>::run(v, sm, t, a.tw_col);
   cp_async_wait_all();
@@ -471,9 +487,11 @@ __global__ void __launch_bounds__(ColCfg<H>::NT) k_col_gs(const __grid_constant_
   });
   if (REPLACE) {
     FftRun<G, true, 1, typename K::Inv>::run(v, sm, t, a.tw_col);
+    const int Wo = opaque(W);
+    float2* fo = opaque(f);
     for_each_slot<G, K::RB>(t, [&](int s, int b, int n) {
       const int col = col0 + b;
-      if (col < W) f[(size_t)n * W + col] = v[s];
+      if (col < Wo) fo[n * Wo + col] = v[s];
     });
   }
   float* dst = a.nmse ? a.nmse + (size_t)a.item_index[k] * a.nmse_stride + a.iter : nullptr;
@@ -530,7 +548,7 @@ __device__ __forceinline__ float2 random_field(uint32_t p, int s, uint64_t seed,
 // FINISH: the field holds rowFFT(h_{s-1} c); accumulate its replay intensity (ACC_READ: add to the
 // stored sum, else start it) and write NMSE[s-1].  START: build subframe s and inverse-transform it.
 template <int H, bool FINISH, bool START>
-__global__ void __launch_bounds__(ColCfg<H>::NT) k_col_ospr(const __grid_constant__ PassArgs a) {
+__global__ void __launch_bounds__(ColCfg<H>::NT, ColCfg<H>::MINB) k_col_ospr(const __grid_constant__ PassArgs a) {
   using K = ColCfg<H>;
   using G = typename K::G;
   extern __shared__ __align__(16) float2 sm[];
@@ -578,9 +596,11 @@ __global__ void __launch_bounds__(ColCfg<H>::NT) k_col_ospr(const __grid_constan
     });
     // the inverse runs the reversed plan: its first radix is the forward plan's last
     FftRun<G, true, 1, typename K::Inv>::run(v, sm, t, a.tw_col);
+    const int Wo = opaque(W);
+    float2* fo = opaque(f);
     for_each_slot<G, K::RB>(t, [&](int s, int b, int n) {
       const int col = col0 + b;
-      if (col < W) f[(size_t)n * W + col] = v[s];
+      if (col < Wo) fo[n * Wo + col] = v[s];
     });
   }
   if (FINISH) {
@@ -780,7 +800,7 @@ __global__ void __launch_bounds__(RowCfg<W>::NT) k_row_mp(const __grid_constant_
 // block stores s_u, sum T^2 and the plane loss, and the last plane the mean loss.  Backward: the
 // adjoint field (2/P) s_u (s_u I - T) / sum T^2 U, inverse column FFTs -> field p (in place).
 template <int H, bool BWD>
-__global__ void __launch_bounds__(ColCfg<H>::NT) k_col_gd(const __grid_constant__ PassArgs a) {
+__global__ void __launch_bounds__(ColCfg<H>::NT, ColCfg<H>::MINB) k_col_gd(const __grid_constant__ PassArgs a) {
   using K = ColCfg<H>;
   using G = typename K::G;
   extern __shared__ __align__(16) float2 sm[];
@@ -839,9 +859,11 @@ __global__ void __launch_bounds__(ColCfg<H>::NT) k_col_gd(const __grid_constant_
       v[s] = gi;
     });
     FftRun<G, true, 1, typename K::Inv>::run(v, sm, t, a.tw_col);
+    const int Wo = opaque(W);
+    float2* fo = opaque(f);
     for_each_slot<G, K::RB>(t, [&](int s, int b, int n) {
       const int col = col0 + b;
-      if (col < W) f[(size_t)n * W + col] = v[s];
+      if (col < Wo) fo[n * Wo + col] = v[s];
     });
   }
 }

@@ -15,7 +15,7 @@
 #include <cstdio>
 #include <mutex>
 
-#include "../../include/hologen.h"
+#include "hologen.h"
 #include "hg_kernels.cuh"
 #include "hg_launch.h"
 
