@@ -185,16 +185,16 @@ HG_API hg_status hg_gd_backward(hg_plan* plan, float* const* phase, const float*
  *
  * Same algorithm, kernels and argument meanings as hg_gs_run with a one-item, one-plane Fourier plan
  * (quant_levels as in hg_plan_desc; target_amp, init_phase, phase_out, level_out are single device
- * pointers; nmse_out is [n_iter + 1]).  Its scratch (field, reduction partials and counter, twiddle
- * and level tables) is a static device array of 8 MiB + 155 KiB that every device which loads this
+ * pointers; nmse_out is [n_iter + 1]).  Its scratch (field, reduction partials, twiddle and level
+ * tables) is a static device array of 8 MiB + 155 KiB that every device which loads this
  * library keeps until the process exits.
  *  - Limits: height * width <= 1048576 pixels, each a supported FFT length; larger sizes return
  *    HG_ERR_UNSUPPORTED_SIZE before anything is launched.
  *  - The first call on a device looks up the array's device address (cudaGetSymbolAddress), so make
  *    that first call before any stream capture.
  *  - Calls no cudaMalloc / cudaFree or allocating routine.  Every call shares the one array and
- *    leaves its contents behind; the call re-initialises what must start fresh (block counter,
- *    tables) on its stream.  Calls that overlap on the GPU (different streams, other host threads)
+ *    leaves its contents behind; each call rewrites the tables and every partial it reads on its own
+ *    stream before using them, so nothing has to start at zero.  Calls that overlap on the GPU (different streams, other host threads)
  *    race on the array and give wrong results: serialise them.
  */
 HG_API hg_status hg_gs_run_noalloc(int32_t height, int32_t width, int32_t quant_levels, const float* target_amp,

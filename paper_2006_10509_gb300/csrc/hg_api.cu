@@ -91,12 +91,13 @@ constexpr int kMaxItems = 256;
 // Kernel kinds for the timing facility.
 enum Kind {
   K_ROW_INIT = 0, K_ROW_GS, K_COL_GS, K_COL_NMSE, K_ROW_FFT, K_COL_FFT, K_ROW_OSPR, K_COL_OSPR,
-  K_ROW_MP_INIT, K_ROW_MP, K_ROW_GD_FWD, K_COL_GD_FWD, K_COL_GD_BWD, K_ROW_GD_BWD, K_AMP_ENERGY, K_NUM_KINDS
+  K_ROW_MP_INIT, K_ROW_MP, K_ROW_GD_FWD, K_COL_GD_FWD, K_COL_GD_BWD, K_ROW_GD_BWD, K_AMP_ENERGY, K_FINALIZE,
+  K_NUM_KINDS
 };
 const char* const kKindNames[K_NUM_KINDS] = {"row_init",   "row_gs",     "col_gs",     "col_nmse",  "row_fft",
                                              "col_fft",    "row_ospr",   "col_ospr",   "row_mp_init", "row_mp",
                                              "row_gd_fwd", "col_gd_fwd", "col_gd_bwd", "row_gd_bwd",
-                                             "amp_energy"};
+                                             "amp_energy", "finalize"};
 constexpr int kMaxLevels = 256;
 
 struct SizeClass {
@@ -105,11 +106,8 @@ struct SizeClass {
   const hg::RowKernels* rk = nullptr;
   const hg::ColKernels* ck = nullptr;
   float2* field = nullptr;       // [slot][plane][H][W]
-  double* partials = nullptr;    // [slot][plane][3 * col_blocks]
-  unsigned* counters = nullptr;  // [slot][plane]
+  float2* partials = nullptr;    // [slot][plane][3 * col_blocks] (hi, lo) pairs
   float* acc = nullptr;          // [slot][H][W] OSPR accumulated intensity (allocated on first use)
-  float* plane_val = nullptr;    // [slot][plane] per-plane NMSE / loss
-  unsigned* plane_counters = nullptr;  // [slot]
   double* stats = nullptr;       // [slot][plane][4] gradient-descent loss statistics
   std::vector<float2*> cx, cy;   // per plane (Fresnel)
   int row_blocks() const { return (H + rk->rows - 1) / rk->rows; }
@@ -307,21 +305,20 @@ void fill_common(const hg_plan* p, const SizeClass& c, int plane, hg::PassArgs& 
   a.lev_phase = p->lev_phase;
   a.field = c.field;
   a.partials = c.partials;
-  a.counters = c.counters;
+  a.col_blocks = c.col_blocks();
   a.n_planes = p->P;
   for (int q = 0; q < p->P; ++q) {
     a.cxp[q] = p->propagation == HG_FRESNEL ? c.cx[q] : nullptr;
     a.cyp[q] = p->propagation == HG_FRESNEL ? c.cy[q] : nullptr;
   }
-  a.plane_val = c.plane_val;
-  a.plane_counters = c.plane_counters;
   a.stats = c.stats;
 }
 
 }  // namespace
 
-// Per (item, plane) amplitude energy of the targets: stats[4 sp + 3] = 1 / sqrt(sum A^2)
-// (multi-plane GS weights each plane's back-propagated field by it).  blockIdx.y = item * P + plane.
+// Per (item, plane) block partials of the target amplitude energy sum A^2 (finalised by
+// k_finalize<2> into stats[4 sp + 3] = 1 / sqrt(sum A^2); multi-plane GS weights each plane's
+// back-propagated field by it).  blockIdx.y = item * P + plane, gridDim.x = column blocks.
 __global__ void k_amp_energy(const __grid_constant__ hg::PassArgs a) {
   const int P = a.n_planes > 1 ? a.n_planes : 1;
   const int k = blockIdx.y / P, p = blockIdx.y % P;
@@ -333,10 +330,7 @@ __global__ void k_amp_energy(const __grid_constant__ hg::PassArgs a) {
     const float x = __ldg(&A[i]);
     e = fmaf(x, x, e);
   }
-  double tot[3];
-  if (hg::block_totals(e, 0.f, 0.f, a.partials + (size_t)sp * 3 * gridDim.x, a.counters + sp, gridDim.x, tot) &&
-      threadIdx.x == 0)
-    a.stats[(size_t)sp * 4 + 3] = tot[0] > 0.0 ? 1.0 / sqrt(tot[0]) : 1.0;
+  hg::block_partials(e, 0.f, 0.f, a.partials + (size_t)sp * 3 * gridDim.x);
 }
 
 namespace {
@@ -476,12 +470,6 @@ hg_status hg_plan_create(const hg_plan_desc* d, hg_plan** out) {
     const size_t n = c.items.size() * (size_t)p->P;
     if ((s = p->alloc(&c.field, n * c.H * c.W, "field workspace")) != HG_OK) return bail(s);
     if ((s = p->alloc(&c.partials, n * 3 * c.col_blocks(), "reduction scratch")) != HG_OK) return bail(s);
-    if ((s = p->alloc(&c.counters, n, "reduction counters")) != HG_OK) return bail(s);
-    if (cudaMemset(c.counters, 0, n * sizeof(unsigned)) != cudaSuccess) return bail(cuda_fail(cudaGetLastError(), "memset"));
-    if ((s = p->alloc(&c.plane_val, n, "plane scratch")) != HG_OK) return bail(s);
-    if ((s = p->alloc(&c.plane_counters, c.items.size(), "plane counters")) != HG_OK) return bail(s);
-    if (cudaMemset(c.plane_counters, 0, c.items.size() * sizeof(unsigned)) != cudaSuccess)
-      return bail(cuda_fail(cudaGetLastError(), "memset"));
     if ((s = p->alloc(&c.stats, n * 4, "loss statistics")) != HG_OK) return bail(s);
     if (cudaMemset(c.stats, 0, n * 4 * sizeof(double)) != cudaSuccess) return bail(cuda_fail(cudaGetLastError(), "memset"));
     for (int pl = 0; pl < p->P; ++pl) {
@@ -639,17 +627,24 @@ hg_status hg_gs_run(hg_plan* p, const float* const* target_amp, const float* con
             a0.level_out[k] = ao.level_out[k];
           }
         }
+        const dim3 gfin(1, nb);
         if ((s = launch(p, K_AMP_ENERGY, (const void*)&k_amp_energy, gcol, 256, 0, a, st)) != HG_OK) return s;
+        if ((s = launch(p, K_FINALIZE, (const void*)&hg::k_finalize<2>, gfin, 32, 0, a, st)) != HG_OK) return s;
         if ((s = launch(p, K_ROW_MP_INIT, c.rk->mp_init[1], grow, c.rk->nt, c.rk->smem, a0, st)) != HG_OK) return s;
         for (int it = 0; it < n_iter; ++it) {
           a.iter = it;
           if ((s = launch(p, K_COL_GS, c.ck->gs[1], gcol, c.ck->nt, c.ck->smem_gs, a, st)) != HG_OK) return s;
           const bool last = it == n_iter - 1;
-          if ((s = launch(p, K_ROW_MP, c.rk->mp[last], grow, c.rk->nt, c.rk->smem, last ? ao : a, st)) != HG_OK)
-            return s;
+          hg::PassArgs ar = last ? ao : a;
+          ar.finalize = nmse_out != nullptr;
+          ar.fin_iter = it;
+          if ((s = launch(p, K_ROW_MP, c.rk->mp[last], grow, c.rk->nt, c.rk->smem, ar, st)) != HG_OK) return s;
         }
         a.iter = n_iter;
+        a.fin_iter = n_iter;
         if ((s = launch(p, K_COL_NMSE, c.ck->gs[0], gcol, c.ck->nt, c.ck->smem_gs, a, st)) != HG_OK) return s;
+        if (nmse_out && (s = launch(p, K_FINALIZE, (const void*)&hg::k_finalize<0>, gfin, 32, 0, a, st)) != HG_OK)
+          return s;
         continue;
       }
       const dim3 grow(c.row_blocks(), nb), gcol(c.col_blocks(), nb);
@@ -672,10 +667,16 @@ hg_status hg_gs_run(hg_plan* p, const float* const* target_amp, const float* con
         a.iter = it;
         if ((s = launch(p, K_COL_GS, c.ck->gs[1], gcol, c.ck->nt, c.ck->smem_gs, a, st)) != HG_OK) return s;
         const bool last = it == n_iter - 1;
-        if ((s = launch(p, K_ROW_GS, c.rk->gs[last], grow, c.rk->nt, c.rk->smem, last ? ao : a, st)) != HG_OK) return s;
+        hg::PassArgs ar = last ? ao : a;
+        ar.finalize = nmse_out != nullptr;  // the row pass first adds up this column pass's NMSE
+        ar.fin_iter = it;
+        if ((s = launch(p, K_ROW_GS, c.rk->gs[last], grow, c.rk->nt, c.rk->smem, ar, st)) != HG_OK) return s;
       }
       a.iter = n_iter;
+      a.fin_iter = n_iter;
       if ((s = launch(p, K_COL_NMSE, c.ck->gs[0], gcol, c.ck->nt, c.ck->smem_gs, a, st)) != HG_OK) return s;
+      if (nmse_out && (s = launch(p, K_FINALIZE, (const void*)&hg::k_finalize<0>, dim3(1, nb), 32, 0, a, st)) != HG_OK)
+        return s;
     }
   }
   return HG_OK;
@@ -730,7 +731,10 @@ hg_status hg_ospr_run(hg_plan* p, const float* const* target_amp, int32_t n_subf
       if ((s = launch(p, K_COL_OSPR, c.ck->ospr[0], gcol, c.ck->nt, c.ck->smem, a, st)) != HG_OK) return s;
       for (int sf = 0; sf < n_subframes; ++sf) {
         a.iter = sf;
-        if ((s = launch(p, K_ROW_OSPR, c.rk->ospr[n_iter == 0], grow, c.rk->nt, rs, a, st)) != HG_OK) return s;
+        hg::PassArgs ar = a;  // the first row pass of subframe sf adds up NMSE[sf - 1]
+        ar.finalize = nmse_out != nullptr && sf > 0;
+        ar.fin_iter = sf - 1;
+        if ((s = launch(p, K_ROW_OSPR, c.rk->ospr[n_iter == 0], grow, c.rk->nt, rs, ar, st)) != HG_OK) return s;
         for (int it = 0; it < n_iter; ++it) {
           if ((s = launch(p, K_COL_GS, c.ck->gs[1], gcol, c.ck->nt, c.ck->smem_gs, ag, st)) != HG_OK) return s;
           if ((s = launch(p, K_ROW_OSPR, c.rk->ospr[it == n_iter - 1], grow, c.rk->nt, rs, a, st)) != HG_OK)
@@ -741,6 +745,9 @@ hg_status hg_ospr_run(hg_plan* p, const float* const* target_amp, int32_t n_subf
         const int variant = sf + 1 < n_subframes ? 1 : 2;
         if ((s = launch(p, K_COL_OSPR, c.ck->ospr[variant], gcol, c.ck->nt, c.ck->smem, a, st)) != HG_OK) return s;
       }
+      a.fin_iter = n_subframes - 1;
+      if (nmse_out && (s = launch(p, K_FINALIZE, (const void*)&hg::k_finalize<0>, dim3(1, nb), 32, 0, a, st)) != HG_OK)
+        return s;
     }
   }
   return HG_OK;
@@ -813,6 +820,7 @@ static hg_status gd_run(hg_plan* p, float* const* phase, const float* const* tar
       if (fwd) {
         if ((s = launch(p, K_ROW_GD_FWD, c.rk->mp_init[0], grow, c.rk->nt, c.rk->smem, a, st)) != HG_OK) return s;
         if ((s = launch(p, K_COL_GD_FWD, c.ck->gd[0], gcol, c.ck->nt, c.ck->smem, a, st)) != HG_OK) return s;
+        if ((s = launch(p, K_FINALIZE, (const void*)&hg::k_finalize<1>, dim3(1, nb), 32, 0, a, st)) != HG_OK) return s;
       }
       if (bwd) {
         if ((s = launch(p, K_COL_GD_BWD, c.ck->gd[1], gcol, c.ck->nt, c.ck->smem, a, st)) != HG_OK) return s;

@@ -116,7 +116,10 @@ struct PassArgs {
   int n_items;
   int H, W;
   int n_levels;            // 0 continuous, 2 binary, N >= 3 N-level
-  int iter;                // iteration index written by column passes (NMSE slot)
+  int iter;                // iteration / subframe index of the pass
+  int col_blocks;          // column-pass blocks per (item, plane): partial triples to add
+  int finalize;            // row passes: 1 = first add up the preceding column pass's NMSE
+  int fin_iter;            // nmse slot of that column pass
   int nmse_stride;         // floats between items in nmse_out (n_iter + 1)
   const float2* tw_row;    // per-stage twiddle tables of length W (TwBlob<W>)
   const float2* tw_col;    // per-stage twiddle tables of length H (TwBlob<H>)
@@ -125,8 +128,7 @@ struct PassArgs {
   const float2* lev;       // level field exp(2 pi i q / N), q < N
   const float* lev_phase;  // level phase 2 pi q / N
   float2* field;           // class field buffer: item k at field + k * H * W
-  double* partials;        // class partial sums: item k at partials + k * 3 * blocks_x
-  unsigned* counters;      // class block counters: one per item
+  float2* partials;        // class partial sums (hi, lo): (slot, plane) at partials + (slot P + p) 3 col_blocks
   float* nmse;             // nmse_out of the run (device) or nullptr
   uint64_t seed;           // starting-phase seed when phase_in is null
   float scale;             // output scale (bare propagation)
@@ -147,8 +149,6 @@ struct PassArgs {
   int n_planes;                        // P (0 is read as 1)
   const float2* cxp[kMaxPlanes];       // per-plane chirp factors (Fresnel)
   const float2* cyp[kMaxPlanes];
-  float* plane_val;                    // class [slot * P + p] per-plane NMSE / loss
-  unsigned* plane_counters;            // class [slot] planes finished
   double* stats;                       // class [slot * P + p][4]: s, sum T^2, loss, 1/sqrt(sum A^2)
   // gradient descent
   float* loss;                         // loss_out [n_items][P + 1] (device) or nullptr
@@ -221,21 +221,40 @@ __device__ __forceinline__ float phase_0_2pi(float2 h) {
   return a;
 }
 
-// Block-wide (ab, bb, tt) sums in double, written as this block's partials; the last block to
-// arrive adds all partials in block order (deterministic).  Returns true in every thread of that
-// last block; its thread 0 receives the totals in tot[0..2].  The block counter is re-armed for the
-// next launch.  No block waits on another.
-__device__ __forceinline__ bool block_totals(float ab, float bb, float tt, double* __restrict__ part,
-                                             unsigned* counter, int nblk, double* tot) {
-  __shared__ double red[3][32];
-  __shared__ bool is_last;
+// ---------------------------------------------------------------- reductions
+//
+// A pass that needs sums over the whole field (NMSE, loss statistics, target energy) only writes
+// per-block partials; the next kernel in stream order (the following row pass, or a small finalise
+// kernel) adds them in block order.  Nothing spins, nothing waits on another block, and the result
+// does not depend on block scheduling.  Within a block the sums run in double-float arithmetic on
+// the FP32 pipes (a pair hi + lo, Knuth's two-sum), which keeps FP64-class accuracy without the
+// low-rate FP64 units.
+
+struct DF {
+  float hi, lo;
+};
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+  const float s = a.hi + b.hi;
+  const float bp = s - a.hi;
+  float e = (a.hi - (s - bp)) + (b.hi - bp);
+  e += a.lo + b.lo;
+  const float h = s + e;
+  return DF{h, e - (h - s)};
+}
+__device__ __forceinline__ DF df_shfl_down(DF v, int o) {
+  return DF{__shfl_down_sync(0xffffffffu, v.hi, o), __shfl_down_sync(0xffffffffu, v.lo, o)};
+}
+
+// Block sums of (x0, x1, x2) -> part[3 * blockIdx.x + i] as (hi, lo) pairs.  All threads must call it.
+__device__ __forceinline__ void block_partials(float x0, float x1, float x2, float2* __restrict__ part) {
+  __shared__ DF red[3][32];
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nw = (blockDim.x + 31) >> 5;
-  double a = ab, b = bb, c = tt;
+  DF a{x0, 0.f}, b{x1, 0.f}, c{x2, 0.f};
 #pragma unroll
   for (int o = 16; o; o >>= 1) {
-    a += __shfl_down_sync(0xffffffffu, a, o);
-    b += __shfl_down_sync(0xffffffffu, b, o);
-    c += __shfl_down_sync(0xffffffffu, c, o);
+    a = df_add(a, df_shfl_down(a, o));
+    b = df_add(b, df_shfl_down(b, o));
+    c = df_add(c, df_shfl_down(c, o));
   }
   if (lane == 0) {
     red[0][warp] = a;
@@ -244,84 +263,98 @@ __device__ __forceinline__ bool block_totals(float ab, float bb, float tt, doubl
   }
   __syncthreads();
   if (warp == 0) {
-    a = lane < nw ? red[0][lane] : 0.0;
-    b = lane < nw ? red[1][lane] : 0.0;
-    c = lane < nw ? red[2][lane] : 0.0;
+    const DF z{0.f, 0.f};
+    a = lane < nw ? red[0][lane] : z;
+    b = lane < nw ? red[1][lane] : z;
+    c = lane < nw ? red[2][lane] : z;
 #pragma unroll
     for (int o = 16; o; o >>= 1) {
-      a += __shfl_down_sync(0xffffffffu, a, o);
-      b += __shfl_down_sync(0xffffffffu, b, o);
-      c += __shfl_down_sync(0xffffffffu, c, o);
+      a = df_add(a, df_shfl_down(a, o));
+      b = df_add(b, df_shfl_down(b, o));
+      c = df_add(c, df_shfl_down(c, o));
     }
     if (lane == 0) {
-      part[3 * blockIdx.x + 0] = a;
-      part[3 * blockIdx.x + 1] = b;
-      part[3 * blockIdx.x + 2] = c;
-      __threadfence();
-      const unsigned prev = atomicAdd(counter, 1u);
-      is_last = (prev == (unsigned)nblk - 1u);
+      part[3 * blockIdx.x + 0] = make_float2(a.hi, a.lo);
+      part[3 * blockIdx.x + 1] = make_float2(b.hi, b.lo);
+      part[3 * blockIdx.x + 2] = make_float2(c.hi, c.lo);
     }
   }
-  __syncthreads();
-  if (!is_last) return false;
-  if (warp == 0) {
-    __threadfence();
-    a = b = c = 0.0;
-    for (int k = lane; k < nblk; k += 32) {
-      a += __ldcg(&part[3 * k + 0]);
-      b += __ldcg(&part[3 * k + 1]);
-      c += __ldcg(&part[3 * k + 2]);
-    }
-#pragma unroll
-    for (int o = 16; o; o >>= 1) {
-      a += __shfl_down_sync(0xffffffffu, a, o);
-      b += __shfl_down_sync(0xffffffffu, b, o);
-      c += __shfl_down_sync(0xffffffffu, c, o);
-    }
-    if (lane == 0) {
-      tot[0] = a;
-      tot[1] = b;
-      tot[2] = c;
-      *counter = 0u;
-    }
-  }
-  return true;
 }
 
-// NMSE = 1 - (sum I T)^2 / (sum I^2 sum T^2) from block_totals' sums.
+// Sums nblk partial triples in a fixed order (lane k takes blocks k, k + 32, ..., then a shuffle
+// tree); call from one full warp; lane 0 receives the totals.
+__device__ __forceinline__ void sum_partials(const float2* __restrict__ part, int nblk, double* tot) {
+  const int lane = threadIdx.x & 31;
+  DF a{0.f, 0.f}, b{0.f, 0.f}, c{0.f, 0.f};
+  for (int k = lane; k < nblk; k += 32) {
+    const float2 x = part[3 * k + 0], y = part[3 * k + 1], z = part[3 * k + 2];
+    a = df_add(a, DF{x.x, x.y});
+    b = df_add(b, DF{y.x, y.y});
+    c = df_add(c, DF{z.x, z.y});
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    a = df_add(a, df_shfl_down(a, o));
+    b = df_add(b, df_shfl_down(b, o));
+    c = df_add(c, df_shfl_down(c, o));
+  }
+  tot[0] = (double)a.hi + (double)a.lo;
+  tot[1] = (double)b.hi + (double)b.lo;
+  tot[2] = (double)c.hi + (double)c.lo;
+}
+
+// NMSE = 1 - (sum I T)^2 / (sum I^2 sum T^2) from the sums (sum I T, sum I^2, sum T^2).
 __device__ __forceinline__ double nmse_of(const double* tot) {
   return (tot[1] > 0.0 && tot[2] > 0.0) ? 1.0 - (tot[0] * tot[0]) / (tot[1] * tot[2]) : 1.0;
 }
 
-// Plane-level step (thread 0 of a plane's last block): stores this plane's value; the last plane
-// of the item to arrive writes the mean over planes (in plane order) to *dst.
-__device__ __forceinline__ void plane_mean(double val, float* vals, unsigned* counter, int P, int p, float* dst) {
-  vals[p] = (float)val;
-  __threadfence();
-  const unsigned prev = atomicAdd(counter, 1u);
-  if (prev == (unsigned)P - 1u) {
-    __threadfence();
-    double m = 0.0;
-    for (int q = 0; q < P; ++q) m += (double)__ldcg(&vals[q]);
-    if (dst) *dst = (float)(m / P);
-    *counter = 0u;
+// NMSE of launch item k from the partials of the preceding column pass (mean over planes), written
+// to nmse[item][fin_iter].  Called by one full warp.
+__device__ __forceinline__ void finalize_nmse(const PassArgs& a, int k) {
+  const int P = a.n_planes > 1 ? a.n_planes : 1;
+  const int slot = a.class_slot[k];
+  double m = 0.0;
+  for (int p = 0; p < P; ++p) {
+    double tot[3];
+    sum_partials(a.partials + ((size_t)slot * P + p) * 3 * a.col_blocks, a.col_blocks, tot);
+    m += nmse_of(tot);
   }
+  if ((threadIdx.x & 31) == 0 && a.nmse) a.nmse[(size_t)a.item_index[k] * a.nmse_stride + a.fin_iter] = (float)(m / P);
 }
 
-// NMSE of one (item, plane) column pass: the last block writes it (P = 1) or folds it into the
-// mean over planes.
-__device__ __forceinline__ void nmse_reduce(float ab, float bb, float tt, const PassArgs& a, int slot, int P, int p,
-                                            float* dst) {
-  const int sp = slot * P + p;
-  double tot[3];
-  if (block_totals(ab, bb, tt, a.partials + (size_t)sp * 3 * gridDim.x, a.counters + sp, gridDim.x, tot) &&
-      threadIdx.x == 0) {
-    if (P == 1) {
-      if (dst) *dst = (float)nmse_of(tot);
-    } else {
-      plane_mean(nmse_of(tot), a.plane_val + (size_t)slot * P, a.plane_counters + slot, P, p, dst);
+// Finalise kernel, one warp per launch item (blockIdx.y).  MODE 0: NMSE of the preceding column
+// pass.  MODE 1: gradient-descent statistics of the forward column pass: per plane s_u = sum I T /
+// sum I^2, sum T^2 and the loss, plus the mean loss.  MODE 2: per-plane target amplitude energy,
+// stats[4 sp + 3] = 1 / sqrt(sum A^2).
+template <int MODE>
+__global__ void __launch_bounds__(32) k_finalize(const __grid_constant__ PassArgs a) {
+  const int k = blockIdx.y;
+  if (MODE == 0) {
+    finalize_nmse(a, k);
+    return;
+  }
+  const int P = a.n_planes > 1 ? a.n_planes : 1;
+  const int slot = a.class_slot[k];
+  double m = 0.0;
+  for (int p = 0; p < P; ++p) {
+    const int sp = slot * P + p;
+    double tot[3];
+    sum_partials(a.partials + (size_t)sp * 3 * a.col_blocks, a.col_blocks, tot);
+    if (threadIdx.x == 0) {
+      double* st = a.stats + (size_t)sp * 4;
+      if (MODE == 1) {
+        const double loss = nmse_of(tot);
+        st[0] = tot[1] > 0.0 ? tot[0] / tot[1] : 0.0;
+        st[1] = tot[2];
+        st[2] = loss;
+        m += loss;
+        if (a.loss) a.loss[(size_t)a.item_index[k] * (P + 1) + p] = (float)loss;
+      } else {
+        st[3] = tot[0] > 0.0 ? 1.0 / sqrt(tot[0]) : 1.0;
+      }
     }
   }
+  if (MODE == 1 && threadIdx.x == 0 && a.loss) a.loss[(size_t)a.item_index[k] * (P + 1) + P] = (float)(m / P);
 }
 
 // ---------------------------------------------------------------- row passes
@@ -377,6 +410,7 @@ __global__ void __launch_bounds__(RowCfg<W>::NT) k_row_gs(const __grid_constant_
   using G = typename K::G;
   extern __shared__ __align__(16) float2 sm[];
   const int t = threadIdx.x, k = blockIdx.y;
+  if (a.finalize && blockIdx.x == 0 && t < 32) finalize_nmse(a, k);
   const int row0 = blockIdx.x * K::ROWS;
   const int H = a.H;
   float2* f = a.field + (size_t)a.class_slot[k] * H * W;
@@ -494,8 +528,7 @@ __global__ void __launch_bounds__(ColCfg<H>::NT, ColCfg<H>::MINB) k_col_gs(const
       if (col < Wo) fo[n * Wo + col] = v[s];
     });
   }
-  float* dst = a.nmse ? a.nmse + (size_t)a.item_index[k] * a.nmse_stride + a.iter : nullptr;
-  nmse_reduce(s_it, s_ii, s_tt, a, slot, P, p, dst);
+  block_partials(s_it, s_ii, s_tt, a.partials + ((size_t)slot * P + p) * 3 * gridDim.x);
 }
 
 // Bare column FFTs (propagation), in place on out: FFT -> (times conj chirp when POST) -> scale.
@@ -603,10 +636,7 @@ __global__ void __launch_bounds__(ColCfg<H>::NT, ColCfg<H>::MINB) k_col_ospr(con
       if (col < Wo) fo[n * Wo + col] = v[s];
     });
   }
-  if (FINISH) {
-    float* dst = a.nmse ? a.nmse + (size_t)a.item_index[k] * a.nmse_stride + (a.iter - 1) : nullptr;
-    nmse_reduce(s_it, s_ii, s_tt, a, slot, 1, 0, dst);
-  }
+  if (FINISH) block_partials(s_it, s_ii, s_tt, a.partials + (size_t)slot * 3 * gridDim.x);
 }
 
 // OSPR row pass: inverse row FFTs, conj chirp, binary projection (bits written LSB-first, 32 pixels
@@ -623,6 +653,7 @@ __global__ void __launch_bounds__(RowCfg<W>::NT) k_row_ospr(const __grid_constan
   const int H = a.H;
   float2* f = a.field + (size_t)a.class_slot[k] * H * W;
   uint32_t* bits = BITS ? a.bits[k] : nullptr;
+  if (a.finalize && blockIdx.x == 0 && t < 32) finalize_nmse(a, k);
   float2 v[K::V];
   for_each_slot<G, K::RE>(t, [&](int s, int b, int n) {
     const int row = row0 + b;
@@ -747,6 +778,7 @@ __global__ void __launch_bounds__(RowCfg<W>::NT) k_row_mp(const __grid_constant_
   extern __shared__ __align__(16) float2 sm[];
   const int P = a.n_planes > 1 ? a.n_planes : 1;
   const int t = threadIdx.x, k = blockIdx.y;
+  if (a.finalize && blockIdx.x == 0 && t < 32) finalize_nmse(a, k);
   const int row0 = blockIdx.x * K::ROWS;
   const int H = a.H;
   const int slot = a.class_slot[k];
@@ -831,18 +863,7 @@ __global__ void __launch_bounds__(ColCfg<H>::NT, ColCfg<H>::MINB) k_col_gd(const
         s_tt = fmaf(tt, tt, s_tt);
       }
     });
-    double tot[3];
-    if (block_totals(s_it, s_ii, s_tt, a.partials + (size_t)sp * 3 * gridDim.x, a.counters + sp, gridDim.x, tot) &&
-        t == 0) {
-      const double loss = nmse_of(tot);
-      double* st = a.stats + (size_t)sp * 4;
-      st[0] = tot[1] > 0.0 ? tot[0] / tot[1] : 0.0;
-      st[1] = tot[2];
-      st[2] = loss;
-      float* lrow = a.loss ? a.loss + (size_t)a.item_index[k] * (P + 1) : nullptr;
-      if (lrow) lrow[p] = (float)loss;
-      plane_mean(loss, a.plane_val + (size_t)slot * P, a.plane_counters + slot, P, p, lrow ? lrow + P : nullptr);
-    }
+    block_partials(s_it, s_ii, s_tt, a.partials + (size_t)sp * 3 * gridDim.x);
   } else {
     const double* st = a.stats + (size_t)sp * 4;
     const float su = (float)__ldcg(&st[0]);

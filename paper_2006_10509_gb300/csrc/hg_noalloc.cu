@@ -4,7 +4,7 @@
 // plug-ins whose host application forbids allocation after start-up, and real-time loops where an
 // allocation (which may synchronise the device) would break the latency budget.  hg_plan_create
 // allocates the field workspace and tables, so those callers cannot use hg_gs_run.  This file gives
-// them one entry point whose scratch -- the field, the reduction partials and counter, and the
+// them one entry point whose scratch -- the field, the reduction partials, and the
 // twiddle and level tables -- lives in a file-scope device array that the CUDA runtime reserves on
 // every device that loads this library, for as long as the process lives.
 //
@@ -25,15 +25,13 @@ namespace {
 // (8 MiB + 155 KiB).
 constexpr size_t kMaxPixels = size_t(1) << 20;
 constexpr size_t kFieldBytes = kMaxPixels * sizeof(float2);  // 8 MiB
-constexpr size_t kPartialBytes = 3 * 1024 * sizeof(double);  // <= 1024 column strips
-constexpr size_t kCounterBytes = 256;
+constexpr size_t kPartialBytes = 3 * 1024 * sizeof(float2);  // <= 1024 column strips
 constexpr int kTwEntries = 8192;                              // per-stage twiddle tables of one length
 constexpr size_t kTwBytes = kTwEntries * sizeof(float2);
 constexpr size_t kLevBytes = 256 * sizeof(float2);
 constexpr size_t kLevPhaseBytes = 256 * sizeof(float);
 constexpr size_t kOffPartials = kFieldBytes;
-constexpr size_t kOffCounter = kOffPartials + kPartialBytes;
-constexpr size_t kOffTwRow = kOffCounter + kCounterBytes;
+constexpr size_t kOffTwRow = kOffPartials + kPartialBytes;
 constexpr size_t kOffTwCol = kOffTwRow + kTwBytes;
 constexpr size_t kOffLev = kOffTwCol + kTwBytes;
 constexpr size_t kOffLevPhase = kOffLev + kLevBytes;
@@ -187,11 +185,6 @@ extern "C" hg_status hg_gs_run_noalloc(int32_t height, int32_t width, int32_t qu
   ck->set_attrs();
   cudaStream_t st = (cudaStream_t)stream;
 
-  // the block counter must start at zero (a call interrupted by a device error could leave it set)
-  if (cudaMemsetAsync(base + kOffCounter, 0, sizeof(unsigned), st) != cudaSuccess) {
-    cudaGetLastError();
-    return err(HG_ERR_CUDA, "counter reset failed");
-  }
   // one thread per table entry (twiddle blobs <= kTwEntries, levels <= 256)
   k_noalloc_tables<<<kTwEntries / 256, 256, 0, st>>>(rk->tw, ck->tw, quant_levels);
   if (cudaGetLastError() != cudaSuccess) return err(HG_ERR_CUDA, "table kernel launch failed");
@@ -207,8 +200,8 @@ extern "C" hg_status hg_gs_run_noalloc(int32_t height, int32_t width, int32_t qu
   a.lev = reinterpret_cast<const float2*>(base + kOffLev);
   a.lev_phase = reinterpret_cast<const float*>(base + kOffLevPhase);
   a.field = reinterpret_cast<float2*>(base);
-  a.partials = reinterpret_cast<double*>(base + kOffPartials);
-  a.counters = reinterpret_cast<unsigned*>(base + kOffCounter);
+  a.partials = reinterpret_cast<float2*>(base + kOffPartials);
+  a.col_blocks = col_blocks;
   a.nmse = nmse_out;
   a.seed = seed;
   a.target[0] = target_amp;
@@ -228,8 +221,13 @@ extern "C" hg_status hg_gs_run_noalloc(int32_t height, int32_t width, int32_t qu
     a.iter = it;
     if ((s = run_kernel(ck->gs[1], gcol, ck->nt, ck->smem_gs, a, st)) != HG_OK) return s;
     const bool last = it == n_iter - 1;
-    if ((s = run_kernel(rk->gs[last], grow, rk->nt, rk->smem, last ? ao : a, st)) != HG_OK) return s;
+    hg::PassArgs ar = last ? ao : a;
+    ar.finalize = nmse_out != nullptr;  // the row pass first adds up this column pass's NMSE
+    ar.fin_iter = it;
+    if ((s = run_kernel(rk->gs[last], grow, rk->nt, rk->smem, ar, st)) != HG_OK) return s;
   }
   a.iter = n_iter;
-  return run_kernel(ck->gs[0], gcol, ck->nt, ck->smem_gs, a, st);
+  a.fin_iter = n_iter;
+  if ((s = run_kernel(ck->gs[0], gcol, ck->nt, ck->smem_gs, a, st)) != HG_OK) return s;
+  return nmse_out ? run_kernel((const void*)&hg::k_finalize<0>, dim3(1, 1), 32, 0, a, st) : HG_OK;
 }
