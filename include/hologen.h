@@ -215,6 +215,18 @@ HG_API hg_status hg_plan_reset_timing(hg_plan* plan);
 HG_API const char* hg_kernel_kind_name(int32_t kind);
 HG_API int64_t hg_plan_launch_count(const hg_plan* plan);
 
+/*
+ * Execution options (no counterpart in the paper, whose batch processing is a job table in the user
+ * interface).  With graph mode on, hg_gs_run captures its whole launch sequence -- every size class,
+ * the classes running concurrently on the plan's own streams -- into a CUDA graph the first time it
+ * sees an argument set, and replays that graph with a single launch while the arguments (pointers,
+ * n_iter, seed) stay the same.  Per-kernel timing is not recorded inside graphs.
+ * hg_plan_item_latency synchronises and returns, for each item, the device time (ms, %globaltimer)
+ * from the start of the last hg_gs_run to the end of its size class.
+ */
+HG_API hg_status hg_plan_set_graph(hg_plan* plan, int32_t enabled);
+HG_API hg_status hg_plan_item_latency(hg_plan* plan, double* ms_out);
+
 /* Human-readable name of a status code (static string). */
 HG_API const char* hg_status_string(hg_status status);
 

@@ -23,7 +23,7 @@ __all__ = [
     "hg_propagate", "hg_gs_run", "hg_status_string", "hg_last_error", "hg_supported_length", "Plan",
     "hg_plan_set_timing", "hg_plan_reset_timing", "hg_plan_kernel_time", "hg_kernel_kind_name",
     "hg_plan_launch_count", "hg_gs_run_noalloc", "hg_ospr_run", "hg_gd_step", "hg_gd_forward",
-    "hg_gd_backward", "hologram_loss",
+    "hg_gd_backward", "hologram_loss", "hg_plan_set_graph", "hg_plan_item_latency",
 ]
 
 HG_OK, HG_ERR_INVALID_ARG, HG_ERR_UNSUPPORTED_SIZE, HG_ERR_OUT_OF_MEMORY = 0, 1, 2, 3
@@ -81,6 +81,8 @@ _SIGNATURES = {
                                            ctypes.POINTER(ctypes.c_int64)]),
     "hg_kernel_kind_name": (ctypes.c_char_p, [ctypes.c_int32]),
     "hg_plan_launch_count": (ctypes.c_int64, [_VP]),
+    "hg_plan_set_graph": (ctypes.c_int, [_VP, ctypes.c_int32]),
+    "hg_plan_item_latency": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double)]),
     "hg_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "hg_last_error": (ctypes.c_char_p, []),
     "hg_supported_length": (ctypes.c_int32, [ctypes.c_int32]),
@@ -286,6 +288,16 @@ def hg_plan_launch_count(plan: int) -> int:
     return int(load().hg_plan_launch_count(plan))
 
 
+def hg_plan_set_graph(plan: int, enabled: bool):
+    _check(load().hg_plan_set_graph(plan, int(bool(enabled))), "hg_plan_set_graph")
+
+
+def hg_plan_item_latency(plan: int, n_items: int) -> list[float]:
+    out = (ctypes.c_double * n_items)()
+    _check(load().hg_plan_item_latency(plan, out), "hg_plan_item_latency")
+    return list(out)
+
+
 class Plan:
     """Owning wrapper around a plan handle (destroyed on close / exit / garbage collection)."""
 
@@ -352,3 +364,9 @@ class Plan:
 
     def launch_count(self) -> int:
         return hg_plan_launch_count(self.handle)
+
+    def set_graph(self, enabled=True):
+        hg_plan_set_graph(self.handle, enabled)
+
+    def item_latency_ms(self) -> list[float]:
+        return hg_plan_item_latency(self.handle, len(self.heights))

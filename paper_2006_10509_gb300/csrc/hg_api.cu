@@ -147,6 +147,16 @@ struct hg_plan {
   float2* lev = nullptr;
   float* lev_phase = nullptr;
   std::vector<void*> allocs;
+  // concurrency, graphs and latency stamps
+  std::vector<cudaStream_t> side;   // one per size class (when there are several)
+  std::vector<cudaEvent_t> join;    // one per size class
+  cudaEvent_t fork = nullptr;
+  unsigned long long* stamps = nullptr;  // [1 + classes]: run start, end of each class (%globaltimer)
+  bool graph = false;
+  cudaStream_t cap = nullptr;       // capture stream of graph mode
+  cudaGraphExec_t gexec = nullptr;
+  std::vector<uintptr_t> gkey;
+  int64_t graph_kernels = 0;
   // timing facility
   bool timing = false;
   int64_t launches = 0;
@@ -160,6 +170,11 @@ struct hg_plan {
   int64_t kind_count[K_NUM_KINDS] = {};
 
   ~hg_plan() {
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (cap) cudaStreamDestroy(cap);
+    for (cudaStream_t q : side) cudaStreamDestroy(q);
+    for (cudaEvent_t e : join) cudaEventDestroy(e);
+    if (fork) cudaEventDestroy(fork);
     for (void* p : allocs) cudaFree(p);
     for (auto& q : pending) {
       cudaEventDestroy(q.a);
@@ -388,6 +403,32 @@ hg_status hg_plan_kernel_time(hg_plan* p, int32_t kind, double* total_ms, int64_
   return HG_OK;
 }
 
+hg_status hg_plan_set_graph(hg_plan* p, int32_t enabled) {
+  if (!p) return fail(HG_ERR_INVALID_ARG, "plan is NULL");
+  p->graph = enabled != 0;
+  if (!p->graph && p->gexec) {
+    DeviceGuard g(p->device);
+    cudaGraphExecDestroy(p->gexec);
+    p->gexec = nullptr;
+    p->gkey.clear();
+  }
+  return HG_OK;
+}
+
+hg_status hg_plan_item_latency(hg_plan* p, double* ms_out) {
+  if (!p) return fail(HG_ERR_INVALID_ARG, "plan is NULL");
+  if (!ms_out) return fail(HG_ERR_INVALID_ARG, "ms_out is NULL");
+  DeviceGuard g(p->device);
+  std::vector<unsigned long long> st(1 + p->classes.size());
+  HG_CUDA(cudaDeviceSynchronize(), "device error");
+  HG_CUDA(cudaMemcpy(st.data(), p->stamps, st.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost), "stamps");
+  for (int i = 0; i < p->n_items; ++i) {
+    const unsigned long long end = st[1 + p->item_class[i]];
+    ms_out[i] = end >= st[0] ? (double)(end - st[0]) * 1e-6 : 0.0;
+  }
+  return HG_OK;
+}
+
 const char* hg_kernel_kind_name(int32_t kind) { return kind >= 0 && kind < K_NUM_KINDS ? kKindNames[kind] : nullptr; }
 
 int64_t hg_plan_launch_count(const hg_plan* p) { return p ? p->launches : 0; }
@@ -507,6 +548,23 @@ hg_status hg_plan_create(const hg_plan_desc* d, hg_plan** out) {
     if ((s = upload(p, &p->lev, lev, "level table")) != HG_OK) return bail(s);
     if ((s = upload(p, &p->lev_phase, ph, "level table")) != HG_OK) return bail(s);
   }
+  if ((s = p->alloc(&p->stamps, 1 + p->classes.size(), "latency stamps")) != HG_OK) return bail(s);
+  if (cudaMemset(p->stamps, 0, (1 + p->classes.size()) * sizeof(unsigned long long)) != cudaSuccess)
+    return bail(cuda_fail(cudaGetLastError(), "memset"));
+  if (p->classes.size() > 1) {
+    if (cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming) != cudaSuccess)
+      return bail(cuda_fail(cudaGetLastError(), "event"));
+    for (size_t i = 0; i < p->classes.size(); ++i) {
+      cudaStream_t q = nullptr;
+      cudaEvent_t e = nullptr;
+      if (cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking) != cudaSuccess)
+        return bail(cuda_fail(cudaGetLastError(), "stream"));
+      p->side.push_back(q);
+      if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+        return bail(cuda_fail(cudaGetLastError(), "event"));
+      p->join.push_back(e);
+    }
+  }
   if (cudaDeviceSynchronize() != cudaSuccess) return bail(cuda_fail(cudaGetLastError(), "plan set-up"));
   *out = p;
   return HG_OK;
@@ -570,6 +628,146 @@ hg_status hg_propagate(hg_plan* p, int32_t plane, int32_t direction, const void*
   return HG_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+struct GsCall {
+  const float* const* target_amp;
+  const float* const* init_phase;
+  uint64_t seed;
+  int32_t n_iter;
+  float* const* phase_out;
+  uint8_t* const* level_out;
+  float* nmse_out;
+};
+
+__global__ void k_stamp(unsigned long long* dst) {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  *dst = t;
+}
+
+// Launch sequence of one size class (every chunk of its items) on stream st.
+hg_status gs_class(hg_plan* p, const SizeClass& c, const GsCall& g, cudaStream_t st) {
+  const float* const* target_amp = g.target_amp;
+  const float* const* init_phase = g.init_phase;
+  const uint64_t seed = g.seed;
+  const int32_t n_iter = g.n_iter;
+  float* const* phase_out = g.phase_out;
+  uint8_t* const* level_out = g.level_out;
+  float* nmse_out = g.nmse_out;
+  hg_status s;
+  const int P = p->P;
+  const int chunk = chunk_items(p);
+  for (size_t c0 = 0; c0 < c.items.size(); c0 += chunk) {
+    const int nb = (int)std::min<size_t>(chunk, c.items.size() - c0);
+    hg::PassArgs a{};
+    fill_common(p, c, 0, a);
+    a.n_items = nb;
+    a.nmse = nmse_out;
+    a.nmse_stride = n_iter + 1;
+    a.seed = seed;
+    for (int k = 0; k < nb; ++k) {
+      const int item = c.items[c0 + k];
+      a.item_index[k] = item;
+      a.class_slot[k] = (int)(c0 + k);
+      for (int q = 0; q < P; ++q) a.target[k * P + q] = target_amp[item * P + q];
+      a.phase_in[k] = init_phase ? init_phase[item] : nullptr;
+    }
+    if (P > 1) {
+      // multi-plane GS: averaged projections over the P planes
+      const dim3 grow(c.row_blocks(), nb), gcol(c.col_blocks(), nb * P);
+      hg::PassArgs a0 = a, ao = a;
+      for (int k = 0; k < nb; ++k) {
+        const int item = c.items[c0 + k];
+        ao.phase_out[k] = phase_out ? phase_out[item] : nullptr;
+        ao.level_out[k] = level_out ? level_out[item] : nullptr;
+        if (n_iter == 0) {
+          a0.phase_out[k] = ao.phase_out[k];
+          a0.level_out[k] = ao.level_out[k];
+        }
+      }
+      const dim3 gfin(1, nb);
+      if ((s = launch(p, K_AMP_ENERGY, (const void*)&k_amp_energy, gcol, 256, 0, a, st)) != HG_OK) return s;
+      if ((s = launch(p, K_FINALIZE, (const void*)&hg::k_finalize<2>, gfin, 32, 0, a, st)) != HG_OK) return s;
+      if ((s = launch(p, K_ROW_MP_INIT, c.rk->mp_init[1], grow, c.rk->nt, c.rk->smem, a0, st)) != HG_OK) return s;
+      for (int it = 0; it < n_iter; ++it) {
+        a.iter = it;
+        if ((s = launch(p, K_COL_GS, c.ck->gs[1], gcol, c.ck->nt, c.ck->smem_gs, a, st)) != HG_OK) return s;
+        const bool last = it == n_iter - 1;
+        hg::PassArgs ar = last ? ao : a;
+        ar.finalize = nmse_out != nullptr;
+        ar.fin_iter = it;
+        if ((s = launch(p, K_ROW_MP, c.rk->mp[last], grow, c.rk->nt, c.rk->smem, ar, st)) != HG_OK) return s;
+      }
+      a.iter = n_iter;
+      a.fin_iter = n_iter;
+      if ((s = launch(p, K_COL_NMSE, c.ck->gs[0], gcol, c.ck->nt, c.ck->smem_gs, a, st)) != HG_OK) return s;
+      if (nmse_out && (s = launch(p, K_FINALIZE, (const void*)&hg::k_finalize<0>, gfin, 32, 0, a, st)) != HG_OK)
+        return s;
+      continue;
+    }
+    const dim3 grow(c.row_blocks(), nb), gcol(c.col_blocks(), nb);
+    // prologue (writes h_0 out when there is no iteration)
+    hg::PassArgs a0 = a;
+    if (n_iter == 0)
+      for (int k = 0; k < nb; ++k) {
+        const int item = c.items[c0 + k];
+        a0.phase_out[k] = phase_out ? phase_out[item] : nullptr;
+        a0.level_out[k] = level_out ? level_out[item] : nullptr;
+      }
+    if ((s = launch(p, K_ROW_INIT, c.rk->init, grow, c.rk->nt, c.rk->smem, a0, st)) != HG_OK) return s;
+    hg::PassArgs ao = a;
+    for (int k = 0; k < nb; ++k) {
+      const int item = c.items[c0 + k];
+      ao.phase_out[k] = phase_out ? phase_out[item] : nullptr;
+      ao.level_out[k] = level_out ? level_out[item] : nullptr;
+    }
+    for (int it = 0; it < n_iter; ++it) {
+      a.iter = it;
+      if ((s = launch(p, K_COL_GS, c.ck->gs[1], gcol, c.ck->nt, c.ck->smem_gs, a, st)) != HG_OK) return s;
+      const bool last = it == n_iter - 1;
+      hg::PassArgs ar = last ? ao : a;
+      ar.finalize = nmse_out != nullptr;  // the row pass first adds up this column pass's NMSE
+      ar.fin_iter = it;
+      if ((s = launch(p, K_ROW_GS, c.rk->gs[last], grow, c.rk->nt, c.rk->smem, ar, st)) != HG_OK) return s;
+    }
+    a.iter = n_iter;
+    a.fin_iter = n_iter;
+    if ((s = launch(p, K_COL_NMSE, c.ck->gs[0], gcol, c.ck->nt, c.ck->smem_gs, a, st)) != HG_OK) return s;
+    if (nmse_out && (s = launch(p, K_FINALIZE, (const void*)&hg::k_finalize<0>, dim3(1, nb), 32, 0, a, st)) != HG_OK)
+      return s;
+  }
+  return HG_OK;
+}
+
+// Every size class of a GS run: classes run concurrently on the plan's side streams (fork / join
+// through events), each bracketed by %globaltimer stamps for the per-hologram latency.
+hg_status gs_enqueue(hg_plan* p, const GsCall& g, cudaStream_t st) {
+  hg_status s;
+  k_stamp<<<1, 1, 0, st>>>(p->stamps);
+  if (p->classes.size() == 1) {
+    if ((s = gs_class(p, p->classes[0], g, st)) != HG_OK) return s;
+    k_stamp<<<1, 1, 0, st>>>(p->stamps + 1);
+    return HG_OK;
+  }
+  HG_CUDA(cudaEventRecord(p->fork, st), "fork");
+  for (size_t i = 0; i < p->classes.size(); ++i) {
+    cudaStream_t side = p->side[i];
+    HG_CUDA(cudaStreamWaitEvent(side, p->fork, 0), "fork");
+    if ((s = gs_class(p, p->classes[i], g, side)) != HG_OK) return s;
+    k_stamp<<<1, 1, 0, side>>>(p->stamps + 1 + i);
+    HG_CUDA(cudaEventRecord(p->join[i], side), "join");
+    HG_CUDA(cudaStreamWaitEvent(st, p->join[i], 0), "join");
+  }
+  return HG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 hg_status hg_gs_run(hg_plan* p, const float* const* target_amp, const float* const* init_phase, uint64_t seed,
                     int32_t n_iter, float* const* phase_out, uint8_t* const* level_out, float* nmse_out,
                     void* stream) {
@@ -595,90 +793,53 @@ hg_status hg_gs_run(hg_plan* p, const float* const* target_amp, const float* con
   if (nmse_out && (s = check_ptr(p, nmse_out, (size_t)p->n_items * (n_iter + 1) * 4, 4, "nmse_out", 0)) != HG_OK)
     return s;
 
+  const GsCall call{target_amp, init_phase, seed, n_iter, phase_out, level_out, nmse_out};
   cudaStream_t st = (cudaStream_t)stream;
-  const int P = p->P;
-  const int chunk = chunk_items(p);
-  for (const SizeClass& c : p->classes) {
-    for (size_t c0 = 0; c0 < c.items.size(); c0 += chunk) {
-      const int nb = (int)std::min<size_t>(chunk, c.items.size() - c0);
-      hg::PassArgs a{};
-      fill_common(p, c, 0, a);
-      a.n_items = nb;
-      a.nmse = nmse_out;
-      a.nmse_stride = n_iter + 1;
-      a.seed = seed;
-      for (int k = 0; k < nb; ++k) {
-        const int item = c.items[c0 + k];
-        a.item_index[k] = item;
-        a.class_slot[k] = (int)(c0 + k);
-        for (int q = 0; q < P; ++q) a.target[k * P + q] = target_amp[item * P + q];
-        a.phase_in[k] = init_phase ? init_phase[item] : nullptr;
-      }
-      if (P > 1) {
-        // multi-plane GS: averaged projections over the P planes
-        const dim3 grow(c.row_blocks(), nb), gcol(c.col_blocks(), nb * P);
-        hg::PassArgs a0 = a, ao = a;
-        for (int k = 0; k < nb; ++k) {
-          const int item = c.items[c0 + k];
-          ao.phase_out[k] = phase_out ? phase_out[item] : nullptr;
-          ao.level_out[k] = level_out ? level_out[item] : nullptr;
-          if (n_iter == 0) {
-            a0.phase_out[k] = ao.phase_out[k];
-            a0.level_out[k] = ao.level_out[k];
-          }
-        }
-        const dim3 gfin(1, nb);
-        if ((s = launch(p, K_AMP_ENERGY, (const void*)&k_amp_energy, gcol, 256, 0, a, st)) != HG_OK) return s;
-        if ((s = launch(p, K_FINALIZE, (const void*)&hg::k_finalize<2>, gfin, 32, 0, a, st)) != HG_OK) return s;
-        if ((s = launch(p, K_ROW_MP_INIT, c.rk->mp_init[1], grow, c.rk->nt, c.rk->smem, a0, st)) != HG_OK) return s;
-        for (int it = 0; it < n_iter; ++it) {
-          a.iter = it;
-          if ((s = launch(p, K_COL_GS, c.ck->gs[1], gcol, c.ck->nt, c.ck->smem_gs, a, st)) != HG_OK) return s;
-          const bool last = it == n_iter - 1;
-          hg::PassArgs ar = last ? ao : a;
-          ar.finalize = nmse_out != nullptr;
-          ar.fin_iter = it;
-          if ((s = launch(p, K_ROW_MP, c.rk->mp[last], grow, c.rk->nt, c.rk->smem, ar, st)) != HG_OK) return s;
-        }
-        a.iter = n_iter;
-        a.fin_iter = n_iter;
-        if ((s = launch(p, K_COL_NMSE, c.ck->gs[0], gcol, c.ck->nt, c.ck->smem_gs, a, st)) != HG_OK) return s;
-        if (nmse_out && (s = launch(p, K_FINALIZE, (const void*)&hg::k_finalize<0>, gfin, 32, 0, a, st)) != HG_OK)
-          return s;
-        continue;
-      }
-      const dim3 grow(c.row_blocks(), nb), gcol(c.col_blocks(), nb);
-      // prologue (writes h_0 out when there is no iteration)
-      hg::PassArgs a0 = a;
-      if (n_iter == 0)
-        for (int k = 0; k < nb; ++k) {
-          const int item = c.items[c0 + k];
-          a0.phase_out[k] = phase_out ? phase_out[item] : nullptr;
-          a0.level_out[k] = level_out ? level_out[item] : nullptr;
-        }
-      if ((s = launch(p, K_ROW_INIT, c.rk->init, grow, c.rk->nt, c.rk->smem, a0, st)) != HG_OK) return s;
-      hg::PassArgs ao = a;
-      for (int k = 0; k < nb; ++k) {
-        const int item = c.items[c0 + k];
-        ao.phase_out[k] = phase_out ? phase_out[item] : nullptr;
-        ao.level_out[k] = level_out ? level_out[item] : nullptr;
-      }
-      for (int it = 0; it < n_iter; ++it) {
-        a.iter = it;
-        if ((s = launch(p, K_COL_GS, c.ck->gs[1], gcol, c.ck->nt, c.ck->smem_gs, a, st)) != HG_OK) return s;
-        const bool last = it == n_iter - 1;
-        hg::PassArgs ar = last ? ao : a;
-        ar.finalize = nmse_out != nullptr;  // the row pass first adds up this column pass's NMSE
-        ar.fin_iter = it;
-        if ((s = launch(p, K_ROW_GS, c.rk->gs[last], grow, c.rk->nt, c.rk->smem, ar, st)) != HG_OK) return s;
-      }
-      a.iter = n_iter;
-      a.fin_iter = n_iter;
-      if ((s = launch(p, K_COL_NMSE, c.ck->gs[0], gcol, c.ck->nt, c.ck->smem_gs, a, st)) != HG_OK) return s;
-      if (nmse_out && (s = launch(p, K_FINALIZE, (const void*)&hg::k_finalize<0>, dim3(1, nb), 32, 0, a, st)) != HG_OK)
-        return s;
-    }
+  if (!p->graph) return gs_enqueue(p, call, st);
+  // graph mode: the whole run is captured once per argument set and replayed with one launch
+  std::vector<uintptr_t> key;
+  key.push_back((uintptr_t)n_iter);
+  key.push_back((uintptr_t)seed);
+  key.push_back((uintptr_t)nmse_out);
+  for (int i = 0; i < p->n_items; ++i) {
+    for (int q = 0; q < p->P; ++q) key.push_back((uintptr_t)target_amp[i * p->P + q]);
+    key.push_back((uintptr_t)(init_phase ? init_phase[i] : nullptr));
+    key.push_back((uintptr_t)(phase_out ? phase_out[i] : nullptr));
+    key.push_back((uintptr_t)(level_out ? level_out[i] : nullptr));
   }
+  if (!p->gexec || key != p->gkey) {
+    if (p->gexec) {
+      cudaGraphExecDestroy(p->gexec);
+      p->gexec = nullptr;
+    }
+    const bool timing = p->timing;
+    const int64_t launches0 = p->launches;
+    p->timing = false;  // no per-kernel events inside a captured graph
+    // captured on the plan's own stream (the caller's may be the legacy default stream, which cannot
+    // be captured); capturing executes nothing, the graph is then launched on the caller's stream
+    if (!p->cap) HG_CUDA(cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking), "capture stream");
+    HG_CUDA(cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal), "graph capture");
+    s = gs_enqueue(p, call, p->cap);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(p->cap, &graph);
+    p->timing = timing;
+    p->graph_kernels = p->launches - launches0;
+    p->launches = launches0;
+    if (s != HG_OK || e != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      return s != HG_OK ? s : cuda_fail(e, "graph capture");
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&p->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) {
+      p->gexec = nullptr;
+      return cuda_fail(ei, "graph instantiate");
+    }
+    p->gkey = key;
+  }
+  HG_CUDA(cudaGraphLaunch(p->gexec, st), "graph launch");
+  p->launches += p->graph_kernels;
   return HG_OK;
 }
 

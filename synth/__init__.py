@@ -40,12 +40,10 @@ MIXED_SIZE_SET = ((512, 512), (1024, 1024), (864, 1536), (2048, 2048), (4096, 40
 
 
 def _circular_blur_axis(x: np.ndarray, w: np.ndarray, axis: int) -> np.ndarray:
-    r = (len(w) - 1) // 2
-    out = np.zeros_like(x)
-    for i, wd in enumerate(w):
-        d = i - r
-        out += wd * np.roll(x, d, axis=axis)
-    return out
+    """Periodic (wrap-around) filtering of x with the symmetric taps w along ``axis``."""
+    from scipy import ndimage
+
+    return ndimage.correlate1d(x, w, axis=axis, mode="wrap")
 
 
 def blur_target(h: int, w: int, sigma: float = 2.0, seed: int = 0) -> np.ndarray:
