@@ -431,12 +431,97 @@ def run_batch(args):
             "px_iter_per_s": px * n_iter / (ms / 1e3), "total_px": px,
             "alg_gbytes_per_batch": 36 * px * n_iter / 1e9,
             "achieved_gb_s": 36 * px * n_iter / (ms / 1e3) / 1e9,
-            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                           "by_size_last_run": {f"{h}x{w}": round(float(np.mean([l for l, sz in zip(lats[-64:], sizes)
+                                                                               if sz == (h, w)])), 3)
+                                                for h, w in sorted(set(sizes))}},
             "sequential_loop_ms": seq_ms, "speedup_vs_loop": seq_ms / ms,
             "final_nmse_median": float(np.median(final_batch)),
             "loop_same_final_nmse": bool(np.array_equal(final_batch, final_loop)),
             "steps": args.steps, "warmup": args.warmup,
             "sizes": {f"{h}x{w}": sum(1 for s in sizes if s == (h, w)) for h, w in sorted(set(sizes))}}
+    print(json.dumps(line))
+
+
+def run_gd(args):
+    """Gradient descent vs multi-plane GS, time to a stated NMSE: 2048^2 phase, Fresnel planes at
+    z = 0.08, 0.10, 0.12 m (532 nm, 8 um pitch), target intensities = squared spot images (seeds
+    4001..4003, unit energy), start phase uniform (seed 4000).  GD: Adam lr 0.05 for up to 200 steps
+    (loss = mean optimal-scale NMSE over planes).  GS: averaged projections, continuous phase, up to
+    1000 iterations, plane-mean NMSE per iterate.  Reported: the time each method needs to reach
+    NMSE 1e-2, 0.1 and the worse method's final NMSE (None where it never does within its budget)."""
+    import numpy as np
+    import torch
+
+    import paper_2006_10509_gb300 as hg
+    import synth
+    from __graft_entry__ import build
+
+    build()
+    dev = torch.device("cuda", 0)
+    n, zs, lam, pitch = 2048, [0.08, 0.10, 0.12], 532e-9, 8e-6
+    ts = []
+    for p in range(3):
+        t = synth.spots_target(n, n, 50, seed=4001 + p).astype(np.float64) ** 2
+        ts.append(torch.from_numpy((t / np.sqrt(np.sum(t * t))).astype(np.float32)).to(dev))
+    amps = [torch.sqrt(t) for t in ts]
+    phi0 = torch.from_numpy(synth.uniform_phase(n, n, seed=4000)).to(dev)
+    kw = dict(propagation=hg.HG_FRESNEL, wavelength_m=lam, pitch_m=pitch, z_m=zs)
+    steps, iters = 200, 1000
+    # gradient descent
+    with hg.Plan([n], [n], **kw) as plan:
+        for _ in range(args.warmup):  # warm-up on a scratch copy
+            ph, m, v = phi0.clone(), torch.zeros_like(phi0), torch.zeros_like(phi0)
+            plan.gd_step([ph], ts, [m], [v], 1, 0.05)
+        ph, m, v = phi0.clone(), torch.zeros_like(phi0), torch.zeros_like(phi0)
+        loss = torch.zeros((steps, 4), dtype=torch.float32, device=dev)
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+        torch.cuda.synchronize()
+        evs[0].record()
+        for k in range(steps):
+            plan.gd_step([ph], ts, [m], [v], k + 1, 0.05, loss_out=loss[k])
+            evs[k + 1].record()
+        torch.cuda.synchronize()
+        gd_t = np.array([evs[0].elapsed_time(e) for e in evs[1:]])  # ms after step k (loss[k] is before it)
+        gd_loss = loss[:, 3].cpu().numpy()
+    # multi-plane GS (same start)
+    with hg.Plan([n], [n], **kw) as plan:
+        nm = torch.zeros((1, iters + 1), dtype=torch.float32, device=dev)
+        for _ in range(args.warmup):
+            plan.gs(amps, 10, init_phase=[phi0], nmse_out=nm[:, :11])
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        plan.gs(amps, iters, init_phase=[phi0], nmse_out=nm)
+        e1.record()
+        torch.cuda.synchronize()
+        gs_ms = e0.elapsed_time(e1)
+        gs_nmse = nm[0].cpu().numpy()
+
+    def first_at(curve, level):
+        idx = np.nonzero(curve <= level)[0]
+        return int(idx[0]) if len(idx) else None
+
+    def times(level):
+        k_gd, k_gs = first_at(gd_loss, level), first_at(gs_nmse, level)
+        # loss[k] is the NMSE of the phase before step k: reached after k steps (end of step k-1)
+        t_gd = None if k_gd is None else (0.0 if k_gd == 0 else float(gd_t[k_gd - 1]))
+        t_gs = None if k_gs is None else k_gs * gs_ms / iters
+        return {"gd_ms": t_gd, "gd_steps": k_gd, "gs_ms": t_gs, "gs_iterations": k_gs,
+                "faster": None if (t_gd is None and t_gs is None) else
+                ("gd" if t_gs is None or (t_gd is not None and t_gd < t_gs) else "gs")}
+
+    gd_final, gs_final = float(gd_loss[-1]), float(gs_nmse[-1])
+    plateau = max(gd_final, gs_final)
+    line = {"workload": "GD (Adam, hand-written adjoint) vs multi-plane GS, 2048^2, 3 Fresnel planes",
+            "metric": "time to NMSE",
+            "time_to": {"0.01": times(1e-2), "0.1": times(0.1), f"worse_final={plateau:.4g}": times(plateau)},
+            "gd": {"ms_per_step": float(gd_t[-1] / steps), "steps": steps, "final_nmse": gd_final,
+                   "alg_gb_s": 172 * n * n / (gd_t[-1] / steps / 1e3) / 1e9},
+            "gs": {"ms_per_iter": gs_ms / iters, "iterations": iters, "final_nmse": gs_final,
+                   "best_nmse": float(gs_nmse.min()), "best_at": int(np.argmin(gs_nmse)),
+                   "alg_gb_s": 108 * n * n / (gs_ms / iters / 1e3) / 1e9},
+            "curves": {"gd_loss_every_20": gd_loss[::20].tolist(), "gs_nmse_every_100": gs_nmse[::100].tolist()}}
     print(json.dumps(line))
 
 
@@ -448,13 +533,17 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-iters", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="gs2048", choices=["gs2048", "batch"],
-                    help="gs2048: the headline line; batch: the mixed-size serving batch")
+    ap.add_argument("--workload", default="gs2048", choices=["gs2048", "batch", "gd"],
+                    help="gs2048: the headline line; batch: the mixed-size serving batch; "
+                         "gd: gradient descent vs multi-plane GS, time to NMSE")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.workload == "batch":
         run_batch(args)
+        return
+    if args.workload == "gd":
+        run_gd(args)
         return
     if args.impl == "reference":
         run_reference(args)

@@ -217,10 +217,11 @@ HG_API int64_t hg_plan_launch_count(const hg_plan* plan);
 
 /*
  * Execution options (no counterpart in the paper, whose batch processing is a job table in the user
- * interface).  With graph mode on, hg_gs_run captures its whole launch sequence -- every size class,
- * the classes running concurrently on the plan's own streams -- into a CUDA graph the first time it
- * sees an argument set, and replays that graph with a single launch while the arguments (pointers,
- * n_iter, seed) stay the same.  Per-kernel timing is not recorded inside graphs.
+ * interface).  hg_gs_run runs the size classes of a plan smallest first (each class one batched
+ * launch per pass), so small holograms finish early.  With graph mode on, it captures the whole launch
+ * sequence into a CUDA graph the first time it sees an argument set, and replays that graph with a
+ * single launch while the arguments (pointers, n_iter, seed) stay the same.  Per-kernel timing is not
+ * recorded inside graphs.
  * hg_plan_item_latency synchronises and returns, for each item, the device time (ms, %globaltimer)
  * from the start of the last hg_gs_run to the end of its size class.
  */

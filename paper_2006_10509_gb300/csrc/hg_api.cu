@@ -6,6 +6,7 @@
 // (twiddle, chirp and level tables; the field workspace; reduction scratch).
 #include <dlfcn.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -147,10 +148,8 @@ struct hg_plan {
   float2* lev = nullptr;
   float* lev_phase = nullptr;
   std::vector<void*> allocs;
-  // concurrency, graphs and latency stamps
-  std::vector<cudaStream_t> side;   // one per size class (when there are several)
-  std::vector<cudaEvent_t> join;    // one per size class
-  cudaEvent_t fork = nullptr;
+  // run order, graphs and latency stamps
+  std::vector<size_t> class_order;  // size classes, smallest first
   unsigned long long* stamps = nullptr;  // [1 + classes]: run start, end of each class (%globaltimer)
   bool graph = false;
   cudaStream_t cap = nullptr;       // capture stream of graph mode
@@ -172,9 +171,6 @@ struct hg_plan {
   ~hg_plan() {
     if (gexec) cudaGraphExecDestroy(gexec);
     if (cap) cudaStreamDestroy(cap);
-    for (cudaStream_t q : side) cudaStreamDestroy(q);
-    for (cudaEvent_t e : join) cudaEventDestroy(e);
-    if (fork) cudaEventDestroy(fork);
     for (void* p : allocs) cudaFree(p);
     for (auto& q : pending) {
       cudaEventDestroy(q.a);
@@ -258,7 +254,7 @@ hg_status launch(hg_plan* p, int kind, const void* fn, dim3 grid, int nt, int sm
     eb = p->get_event();
     if (ea && eb) cudaEventRecord(ea, s);
   }
-  cudaError_t e = cudaLaunchKernel(fn, grid, dim3(nt), args, (size_t)smem, s);
+  const cudaError_t e = cudaLaunchKernel(fn, grid, dim3(nt), args, (size_t)smem, s);
   if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
   p->launches++;
   if (ea && eb) {
@@ -551,20 +547,11 @@ hg_status hg_plan_create(const hg_plan_desc* d, hg_plan** out) {
   if ((s = p->alloc(&p->stamps, 1 + p->classes.size(), "latency stamps")) != HG_OK) return bail(s);
   if (cudaMemset(p->stamps, 0, (1 + p->classes.size()) * sizeof(unsigned long long)) != cudaSuccess)
     return bail(cuda_fail(cudaGetLastError(), "memset"));
-  if (p->classes.size() > 1) {
-    if (cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming) != cudaSuccess)
-      return bail(cuda_fail(cudaGetLastError(), "event"));
-    for (size_t i = 0; i < p->classes.size(); ++i) {
-      cudaStream_t q = nullptr;
-      cudaEvent_t e = nullptr;
-      if (cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking) != cudaSuccess)
-        return bail(cuda_fail(cudaGetLastError(), "stream"));
-      p->side.push_back(q);
-      if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
-        return bail(cuda_fail(cudaGetLastError(), "event"));
-      p->join.push_back(e);
-    }
-  }
+  p->class_order.resize(p->classes.size());
+  for (size_t i = 0; i < p->classes.size(); ++i) p->class_order[i] = i;
+  std::stable_sort(p->class_order.begin(), p->class_order.end(), [&](size_t x, size_t y) {
+    return (size_t)p->classes[x].H * p->classes[x].W < (size_t)p->classes[y].H * p->classes[y].W;
+  });
   if (cudaDeviceSynchronize() != cudaSuccess) return bail(cuda_fail(cudaGetLastError(), "plan set-up"));
   *out = p;
   return HG_OK;
@@ -742,24 +729,15 @@ hg_status gs_class(hg_plan* p, const SizeClass& c, const GsCall& g, cudaStream_t
   return HG_OK;
 }
 
-// Every size class of a GS run: classes run concurrently on the plan's side streams (fork / join
-// through events), each bracketed by %globaltimer stamps for the per-hologram latency.
+// Every size class of a GS run, smallest holograms first (shortest job first: batched launches keep
+// the GPU full either way, and small holograms then finish early), each followed by a %globaltimer
+// stamp for the per-hologram latency.
 hg_status gs_enqueue(hg_plan* p, const GsCall& g, cudaStream_t st) {
   hg_status s;
   k_stamp<<<1, 1, 0, st>>>(p->stamps);
-  if (p->classes.size() == 1) {
-    if ((s = gs_class(p, p->classes[0], g, st)) != HG_OK) return s;
-    k_stamp<<<1, 1, 0, st>>>(p->stamps + 1);
-    return HG_OK;
-  }
-  HG_CUDA(cudaEventRecord(p->fork, st), "fork");
-  for (size_t i = 0; i < p->classes.size(); ++i) {
-    cudaStream_t side = p->side[i];
-    HG_CUDA(cudaStreamWaitEvent(side, p->fork, 0), "fork");
-    if ((s = gs_class(p, p->classes[i], g, side)) != HG_OK) return s;
-    k_stamp<<<1, 1, 0, side>>>(p->stamps + 1 + i);
-    HG_CUDA(cudaEventRecord(p->join[i], side), "join");
-    HG_CUDA(cudaStreamWaitEvent(st, p->join[i], 0), "join");
+  for (size_t i : p->class_order) {
+    if ((s = gs_class(p, p->classes[i], g, st)) != HG_OK) return s;
+    k_stamp<<<1, 1, 0, st>>>(p->stamps + 1 + i);
   }
   return HG_OK;
 }
