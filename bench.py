@@ -443,6 +443,75 @@ def run_batch(args):
     print(json.dumps(line))
 
 
+def run_config(args):
+    """The remaining single-GPU configurations, each timed over graph replays after warm-up:
+    gs256:       Fourier GS 256^2, continuous, 20 iterations, smoothed-noise target (seed 1001), start
+                 phase seed 1002 (latency-bound: the whole field is 512 KB).
+    fresnel1024: Fresnel GS 1024^2 (532 nm, 8 um, z = 0.1 m), 8-level, 100 iterations, 50-spot target
+                 (seed 2001), start phase seed 2002.
+    ospr:        OSPR 1920x1080 (W x H), 16 point-symmetric smoothed-noise targets (seeds 3001..3016),
+                 24 binary subframes each, Philox seed 3000, the whole batch as one graph launch."""
+    import numpy as np
+    import torch
+
+    import paper_2006_10509_gb300 as hg
+    import synth
+    from __graft_entry__ import build
+
+    build()
+    dev = torch.device("cuda", 0)
+    w = args.workload
+    if w == "gs256":
+        h = wd = 256
+        n_iter = 20
+        a = torch.from_numpy(synth.blur_target(h, wd, SIGMA, seed=1001)).to(dev)
+        p0 = torch.from_numpy(synth.uniform_phase(h, wd, seed=1002)).to(dev)
+        plan = hg.Plan([h], [wd])
+        nm = torch.zeros((1, n_iter + 1), dtype=torch.float32, device=dev)
+        run = lambda: plan.gs([a], n_iter, init_phase=[p0], nmse_out=nm)  # noqa: E731
+        units, unit, bpu = n_iter, "it/s", 36 * h * wd
+    elif w == "fresnel1024":
+        h = wd = 1024
+        n_iter = 100
+        a = torch.from_numpy(synth.spots_target(h, wd, 50, seed=2001)).to(dev)
+        p0 = torch.from_numpy(synth.uniform_phase(h, wd, seed=2002)).to(dev)
+        plan = hg.Plan([h], [wd], propagation=hg.HG_FRESNEL, wavelength_m=532e-9, pitch_m=8e-6, z_m=[0.1],
+                       quant_levels=8)
+        nm = torch.zeros((1, n_iter + 1), dtype=torch.float32, device=dev)
+        run = lambda: plan.gs([a], n_iter, init_phase=[p0], nmse_out=nm)  # noqa: E731
+        units, unit, bpu = n_iter, "it/s", 36 * h * wd
+    else:
+        h, wd, nt, ns = 1080, 1920, 16, 24
+        ts = [torch.from_numpy(synth.symmetrise(synth.blur_target(h, wd, SIGMA, seed=3001 + k))).to(dev)
+              for k in range(nt)]
+        bits = [torch.zeros((ns, h, (wd + 31) // 32), dtype=torch.int32, device=dev) for _ in range(nt)]
+        plan = hg.Plan([h] * nt, [wd] * nt, quant_levels=2)
+        nm = torch.zeros((nt, ns), dtype=torch.float32, device=dev)
+        run = lambda: plan.ospr(ts, ns, 0, 3000, bits_out=bits, nmse_out=nm)  # noqa: E731
+        units, unit, bpu = nt * ns, "subframes/s", 44 * h * wd
+    plan.set_graph(True)
+    for _ in range(args.warmup):
+        run()
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        run()
+        e1.record()
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    ms = statistics.median(times)
+    peak, src = measured_peaks()
+    gbs = bpu * units / (ms / 1e3) / 1e9
+    line = {"workload": w, "value": units / (ms / 1e3), "unit": unit, "ms_per_run": ms,
+            "alg_bytes_per_unit": bpu, "achieved_gb_s": gbs, "frac_of_hbm": gbs / peak, "peak_source": src,
+            "final_nmse": nm.cpu().numpy()[:, -1].tolist()[:4], "steps": args.steps, "warmup": args.warmup,
+            "graph": True}
+    plan.close()
+    print(json.dumps(line))
+
+
 def run_gd(args):
     """Gradient descent vs multi-plane GS, time to a stated NMSE: 2048^2 phase, Fresnel planes at
     z = 0.08, 0.10, 0.12 m (532 nm, 8 um pitch), target intensities = squared spot images (seeds
@@ -533,9 +602,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-iters", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="gs2048", choices=["gs2048", "batch", "gd"],
+    ap.add_argument("--workload", default="gs2048",
+                    choices=["gs2048", "batch", "gd", "gs256", "fresnel1024", "ospr"],
                     help="gs2048: the headline line; batch: the mixed-size serving batch; "
-                         "gd: gradient descent vs multi-plane GS, time to NMSE")
+                         "gd: gradient descent vs multi-plane GS, time to NMSE; gs256 / fresnel1024 / ospr: "
+                         "the other single-GPU configurations")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -544,6 +615,9 @@ def main():
         return
     if args.workload == "gd":
         run_gd(args)
+        return
+    if args.workload in ("gs256", "fresnel1024", "ospr"):
+        run_config(args)
         return
     if args.impl == "reference":
         run_reference(args)

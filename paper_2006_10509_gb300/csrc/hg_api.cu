@@ -11,6 +11,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <string>
 #include <vector>
@@ -742,6 +743,47 @@ hg_status gs_enqueue(hg_plan* p, const GsCall& g, cudaStream_t st) {
   return HG_OK;
 }
 
+// Runs enqueue(stream) directly, or -- in graph mode -- replays the CUDA graph captured for this
+// argument key (capturing it first when the key is new).  Capture happens on the plan's own stream
+// (the caller's may be the legacy default stream, which cannot be captured); capturing executes
+// nothing, and the graph is launched on the caller's stream.
+hg_status run_maybe_graph(hg_plan* p, const std::vector<uintptr_t>& key,
+                          const std::function<hg_status(cudaStream_t)>& enqueue, cudaStream_t st) {
+  if (!p->graph) return enqueue(st);
+  if (!p->gexec || key != p->gkey) {
+    if (p->gexec) {
+      cudaGraphExecDestroy(p->gexec);
+      p->gexec = nullptr;
+    }
+    const bool timing = p->timing;
+    const int64_t launches0 = p->launches;
+    p->timing = false;  // no per-kernel events inside a captured graph
+    if (!p->cap) HG_CUDA(cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking), "capture stream");
+    HG_CUDA(cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal), "graph capture");
+    const hg_status s = enqueue(p->cap);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(p->cap, &graph);
+    p->timing = timing;
+    p->graph_kernels = p->launches - launches0;
+    p->launches = launches0;
+    if (s != HG_OK || e != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      return s != HG_OK ? s : cuda_fail(e, "graph capture");
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&p->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) {
+      p->gexec = nullptr;
+      return cuda_fail(ei, "graph instantiate");
+    }
+    p->gkey = key;
+  }
+  HG_CUDA(cudaGraphLaunch(p->gexec, st), "graph launch");
+  p->launches += p->graph_kernels;
+  return HG_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -772,53 +814,15 @@ hg_status hg_gs_run(hg_plan* p, const float* const* target_amp, const float* con
     return s;
 
   const GsCall call{target_amp, init_phase, seed, n_iter, phase_out, level_out, nmse_out};
-  cudaStream_t st = (cudaStream_t)stream;
-  if (!p->graph) return gs_enqueue(p, call, st);
-  // graph mode: the whole run is captured once per argument set and replayed with one launch
-  std::vector<uintptr_t> key;
-  key.push_back((uintptr_t)n_iter);
-  key.push_back((uintptr_t)seed);
-  key.push_back((uintptr_t)nmse_out);
-  for (int i = 0; i < p->n_items; ++i) {
-    for (int q = 0; q < p->P; ++q) key.push_back((uintptr_t)target_amp[i * p->P + q]);
-    key.push_back((uintptr_t)(init_phase ? init_phase[i] : nullptr));
-    key.push_back((uintptr_t)(phase_out ? phase_out[i] : nullptr));
-    key.push_back((uintptr_t)(level_out ? level_out[i] : nullptr));
-  }
-  if (!p->gexec || key != p->gkey) {
-    if (p->gexec) {
-      cudaGraphExecDestroy(p->gexec);
-      p->gexec = nullptr;
+  std::vector<uintptr_t> key{1, (uintptr_t)n_iter, (uintptr_t)seed, (uintptr_t)nmse_out};
+  if (p->graph)
+    for (int i = 0; i < p->n_items; ++i) {
+      for (int q = 0; q < p->P; ++q) key.push_back((uintptr_t)target_amp[i * p->P + q]);
+      key.push_back((uintptr_t)(init_phase ? init_phase[i] : nullptr));
+      key.push_back((uintptr_t)(phase_out ? phase_out[i] : nullptr));
+      key.push_back((uintptr_t)(level_out ? level_out[i] : nullptr));
     }
-    const bool timing = p->timing;
-    const int64_t launches0 = p->launches;
-    p->timing = false;  // no per-kernel events inside a captured graph
-    // captured on the plan's own stream (the caller's may be the legacy default stream, which cannot
-    // be captured); capturing executes nothing, the graph is then launched on the caller's stream
-    if (!p->cap) HG_CUDA(cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking), "capture stream");
-    HG_CUDA(cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal), "graph capture");
-    s = gs_enqueue(p, call, p->cap);
-    cudaGraph_t graph = nullptr;
-    const cudaError_t e = cudaStreamEndCapture(p->cap, &graph);
-    p->timing = timing;
-    p->graph_kernels = p->launches - launches0;
-    p->launches = launches0;
-    if (s != HG_OK || e != cudaSuccess) {
-      if (graph) cudaGraphDestroy(graph);
-      cudaGetLastError();
-      return s != HG_OK ? s : cuda_fail(e, "graph capture");
-    }
-    const cudaError_t ei = cudaGraphInstantiate(&p->gexec, graph, 0);
-    cudaGraphDestroy(graph);
-    if (ei != cudaSuccess) {
-      p->gexec = nullptr;
-      return cuda_fail(ei, "graph instantiate");
-    }
-    p->gkey = key;
-  }
-  HG_CUDA(cudaGraphLaunch(p->gexec, st), "graph launch");
-  p->launches += p->graph_kernels;
-  return HG_OK;
+  return run_maybe_graph(p, key, [&](cudaStream_t q) { return gs_enqueue(p, call, q); }, (cudaStream_t)stream);
 }
 
 hg_status hg_ospr_run(hg_plan* p, const float* const* target_amp, int32_t n_subframes, int32_t n_iter,
@@ -843,53 +847,62 @@ hg_status hg_ospr_run(hg_plan* p, const float* const* target_amp, int32_t n_subf
     if (!c.acc && (s = p->alloc(&c.acc, c.items.size() * (size_t)c.H * c.W, "OSPR intensity buffer")) != HG_OK)
       return s;
 
-  cudaStream_t st = (cudaStream_t)stream;
-  for (const SizeClass& c : p->classes) {
-    for (size_t c0 = 0; c0 < c.items.size(); c0 += hg::kMaxBatch) {
-      const int nb = (int)std::min<size_t>(hg::kMaxBatch, c.items.size() - c0);
-      hg::PassArgs a{};
-      fill_common(p, c, 0, a);
-      a.n_levels = 2;
-      a.n_items = nb;
-      a.acc = c.acc;
-      a.nmse_stride = n_subframes;
-      a.seed = seed;
-      for (int k = 0; k < nb; ++k) {
-        const int item = c.items[c0 + k];
-        a.item_index[k] = item;
-        a.class_slot[k] = (int)(c0 + k);
-        a.target[k] = target_amp[item];
-        a.bits[k] = bits_out ? bits_out[item] : nullptr;
-      }
-      hg::PassArgs ag = a;  // binary GS refinements inside a subframe: no NMSE, no bits
-      ag.nmse = nullptr;
-      a.nmse = nmse_out;
-      const dim3 grow(c.row_blocks(), nb), gcol(c.col_blocks(), nb);
-      const int rs = c.rk->smem_ospr;
-      a.iter = 0;
-      if ((s = launch(p, K_COL_OSPR, c.ck->ospr[0], gcol, c.ck->nt, c.ck->smem, a, st)) != HG_OK) return s;
-      for (int sf = 0; sf < n_subframes; ++sf) {
-        a.iter = sf;
-        hg::PassArgs ar = a;  // the first row pass of subframe sf adds up NMSE[sf - 1]
-        ar.finalize = nmse_out != nullptr && sf > 0;
-        ar.fin_iter = sf - 1;
-        if ((s = launch(p, K_ROW_OSPR, c.rk->ospr[n_iter == 0], grow, c.rk->nt, rs, ar, st)) != HG_OK) return s;
-        for (int it = 0; it < n_iter; ++it) {
-          if ((s = launch(p, K_COL_GS, c.ck->gs[1], gcol, c.ck->nt, c.ck->smem_gs, ag, st)) != HG_OK) return s;
-          if ((s = launch(p, K_ROW_OSPR, c.rk->ospr[it == n_iter - 1], grow, c.rk->nt, rs, a, st)) != HG_OK)
-            return s;
-        }
-        a.iter = sf + 1;
-        a.acc_read = sf > 0;
-        const int variant = sf + 1 < n_subframes ? 1 : 2;
-        if ((s = launch(p, K_COL_OSPR, c.ck->ospr[variant], gcol, c.ck->nt, c.ck->smem, a, st)) != HG_OK) return s;
-      }
-      a.fin_iter = n_subframes - 1;
-      if (nmse_out && (s = launch(p, K_FINALIZE, (const void*)&hg::k_finalize<0>, dim3(1, nb), 32, 0, a, st)) != HG_OK)
-        return s;
+  std::vector<uintptr_t> key{2, (uintptr_t)n_subframes, (uintptr_t)n_iter, (uintptr_t)seed, (uintptr_t)nmse_out};
+  if (p->graph)
+    for (int i = 0; i < p->n_items; ++i) {
+      key.push_back((uintptr_t)target_amp[i]);
+      key.push_back((uintptr_t)(bits_out ? bits_out[i] : nullptr));
     }
-  }
-  return HG_OK;
+  auto enqueue = [&](cudaStream_t st) -> hg_status {
+    hg_status s;
+    for (const SizeClass& c : p->classes) {
+      for (size_t c0 = 0; c0 < c.items.size(); c0 += hg::kMaxBatch) {
+        const int nb = (int)std::min<size_t>(hg::kMaxBatch, c.items.size() - c0);
+        hg::PassArgs a{};
+        fill_common(p, c, 0, a);
+        a.n_levels = 2;
+        a.n_items = nb;
+        a.acc = c.acc;
+        a.nmse_stride = n_subframes;
+        a.seed = seed;
+        for (int k = 0; k < nb; ++k) {
+          const int item = c.items[c0 + k];
+          a.item_index[k] = item;
+          a.class_slot[k] = (int)(c0 + k);
+          a.target[k] = target_amp[item];
+          a.bits[k] = bits_out ? bits_out[item] : nullptr;
+        }
+        hg::PassArgs ag = a;  // binary GS refinements inside a subframe: no NMSE, no bits
+        ag.nmse = nullptr;
+        a.nmse = nmse_out;
+        const dim3 grow(c.row_blocks(), nb), gcol(c.col_blocks(), nb);
+        const int rs = c.rk->smem_ospr;
+        a.iter = 0;
+        if ((s = launch(p, K_COL_OSPR, c.ck->ospr[0], gcol, c.ck->nt, c.ck->smem, a, st)) != HG_OK) return s;
+        for (int sf = 0; sf < n_subframes; ++sf) {
+          a.iter = sf;
+          hg::PassArgs ar = a;  // the first row pass of subframe sf adds up NMSE[sf - 1]
+          ar.finalize = nmse_out != nullptr && sf > 0;
+          ar.fin_iter = sf - 1;
+          if ((s = launch(p, K_ROW_OSPR, c.rk->ospr[n_iter == 0], grow, c.rk->nt, rs, ar, st)) != HG_OK) return s;
+          for (int it = 0; it < n_iter; ++it) {
+            if ((s = launch(p, K_COL_GS, c.ck->gs[1], gcol, c.ck->nt, c.ck->smem_gs, ag, st)) != HG_OK) return s;
+            if ((s = launch(p, K_ROW_OSPR, c.rk->ospr[it == n_iter - 1], grow, c.rk->nt, rs, a, st)) != HG_OK)
+              return s;
+          }
+          a.iter = sf + 1;
+          a.acc_read = sf > 0;
+          const int variant = sf + 1 < n_subframes ? 1 : 2;
+          if ((s = launch(p, K_COL_OSPR, c.ck->ospr[variant], gcol, c.ck->nt, c.ck->smem, a, st)) != HG_OK) return s;
+        }
+        a.fin_iter = n_subframes - 1;
+        if (nmse_out && (s = launch(p, K_FINALIZE, (const void*)&hg::k_finalize<0>, dim3(1, nb), 32, 0, a, st)) != HG_OK)
+          return s;
+      }
+    }
+    return HG_OK;
+  };
+  return run_maybe_graph(p, key, enqueue, (cudaStream_t)stream);
 }
 
 // Shared driver of the gradient-descent calls.  FWD: forward row pass (h = e^{i phi}, per-plane row
