@@ -161,6 +161,11 @@ def barrier(ws):
         dist.barrier()
 
 
+def rank_seeds(rank: int) -> tuple[int, int]:
+    """Seeds of the hologram a rank runs (target, starting phase): every rank has its own hologram."""
+    return 0 + rank, 1 + rank
+
+
 def max_over_ranks(x: float, ws: int, dev) -> float:
     if ws == 1:
         return x
@@ -258,8 +263,9 @@ def run_ours(args):
     barrier(ws)
     build()
 
-    a_host = torch.from_numpy(synth.blur_target(H, W, SIGMA, seed=0 + rank)).pin_memory()
-    p_host = torch.from_numpy(synth.uniform_phase(H, W, seed=1 + rank)).pin_memory()
+    seed_t, seed_p = rank_seeds(rank)
+    a_host = torch.from_numpy(synth.blur_target(H, W, SIGMA, seed=seed_t)).pin_memory()
+    p_host = torch.from_numpy(synth.uniform_phase(H, W, seed=seed_p)).pin_memory()
     a = a_host.to(dev)
     p = p_host.to(dev)
     nm = torch.zeros((1, N_ITER + 1), dtype=torch.float32, device=dev)
