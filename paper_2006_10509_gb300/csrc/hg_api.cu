@@ -94,12 +94,12 @@ constexpr int kMaxItems = 256;
 enum Kind {
   K_ROW_INIT = 0, K_ROW_GS, K_COL_GS, K_COL_NMSE, K_ROW_FFT, K_COL_FFT, K_ROW_OSPR, K_COL_OSPR,
   K_ROW_MP_INIT, K_ROW_MP, K_ROW_GD_FWD, K_COL_GD_FWD, K_COL_GD_BWD, K_ROW_GD_BWD, K_AMP_ENERGY, K_FINALIZE,
-  K_NUM_KINDS
+  K_TILE_TARGET, K_NUM_KINDS
 };
 const char* const kKindNames[K_NUM_KINDS] = {"row_init",   "row_gs",     "col_gs",     "col_nmse",  "row_fft",
                                              "col_fft",    "row_ospr",   "col_ospr",   "row_mp_init", "row_mp",
                                              "row_gd_fwd", "col_gd_fwd", "col_gd_bwd", "row_gd_bwd",
-                                             "amp_energy", "finalize"};
+                                             "amp_energy", "finalize", "tile_target"};
 constexpr int kMaxLevels = 256;
 
 struct SizeClass {
@@ -110,6 +110,7 @@ struct SizeClass {
   float2* field = nullptr;       // [slot][plane][H][W]
   float2* partials = nullptr;    // [slot][plane][3 * col_blocks] (hi, lo) pairs
   float* acc = nullptr;          // [slot][H][W] OSPR accumulated intensity (allocated on first use)
+  float* ttile = nullptr;        // [slot][plane][strip][H][C] targets re-laid out for the GS column passes
   double* stats = nullptr;       // [slot][plane][4] gradient-descent loss statistics
   std::vector<float2*> cx, cy;   // per plane (Fresnel)
   int row_blocks() const { return (H + rk->rows - 1) / rk->rows; }
@@ -247,8 +248,9 @@ hg_status check_ptr(const hg_plan* p, const void* ptr, size_t bytes, size_t alig
 }
 
 hg_status launch(hg_plan* p, int kind, const void* fn, dim3 grid, int nt, int smem, const hg::PassArgs& a,
-                 cudaStream_t s) {
-  void* args[] = {(void*)&a};
+                 cudaStream_t s, int extra_int = 0, float* extra_ptr = nullptr) {
+  void* args3[] = {(void*)&a, (void*)&extra_int, (void*)&extra_ptr};
+  void** args = args3;  // kernels with one parameter read only the first entry
   cudaEvent_t ea = nullptr, eb = nullptr;
   if (p->timing) {
     ea = p->get_event();
@@ -327,6 +329,21 @@ void fill_common(const hg_plan* p, const SizeClass& c, int plane, hg::PassArgs& 
 }
 
 }  // namespace
+
+// Re-lays the targets out per column strip for the GS column passes: strip t of (item, plane) holds
+// [H][C] contiguous (zero past W), so a column pass streams its strip with contiguous copies instead
+// of C-float pieces of every row.  blockIdx.x = strip, blockIdx.y = item * P + plane.
+__global__ void k_tile_target(const __grid_constant__ hg::PassArgs a, int C, float* ttile) {
+  const int P = a.n_planes > 1 ? a.n_planes : 1;
+  const int k = blockIdx.y / P, p = blockIdx.y % P;
+  const float* A = a.target[k * P + p];
+  const int H = a.H, W = a.W, col0 = blockIdx.x * C;
+  float* dst = ttile + (((size_t)a.class_slot[k] * P + p) * gridDim.x + blockIdx.x) * (size_t)H * C;
+  for (int i = threadIdx.x; i < H * C; i += blockDim.x) {
+    const int n = i / C, b = i % C;
+    dst[i] = col0 + b < W ? __ldg(&A[(size_t)n * W + col0 + b]) : 0.f;
+  }
+}
 
 // Per (item, plane) block partials of the target amplitude energy sum A^2 (finalised by
 // k_finalize<2> into stats[4 sp + 3] = 1 / sqrt(sum A^2); multi-plane GS weights each plane's
@@ -509,6 +526,8 @@ hg_status hg_plan_create(const hg_plan_desc* d, hg_plan** out) {
     if ((s = p->alloc(&c.field, n * c.H * c.W, "field workspace")) != HG_OK) return bail(s);
     if ((s = p->alloc(&c.partials, n * 3 * c.col_blocks(), "reduction scratch")) != HG_OK) return bail(s);
     if ((s = p->alloc(&c.stats, n * 4, "loss statistics")) != HG_OK) return bail(s);
+    if ((s = p->alloc(&c.ttile, n * c.col_blocks() * (size_t)c.H * c.ck->cols, "target tiles")) != HG_OK)
+      return bail(s);
     if (cudaMemset(c.stats, 0, n * 4 * sizeof(double)) != cudaSuccess) return bail(cuda_fail(cudaGetLastError(), "memset"));
     for (int pl = 0; pl < p->P; ++pl) {
       float2 *cx = nullptr, *cy = nullptr;
@@ -663,6 +682,11 @@ hg_status gs_class(hg_plan* p, const SizeClass& c, const GsCall& g, cudaStream_t
       for (int q = 0; q < P; ++q) a.target[k * P + q] = target_amp[item * P + q];
       a.phase_in[k] = init_phase ? init_phase[item] : nullptr;
     }
+    // targets re-laid out per column strip once per run (read by every column pass of the run)
+    if ((s = launch(p, K_TILE_TARGET, (const void*)&k_tile_target, dim3(c.col_blocks(), nb * P), 256, 0, a, st,
+                    c.ck->cols, c.ttile)) != HG_OK)
+      return s;
+    a.ttile = c.ttile;
     if (P > 1) {
       // multi-plane GS: averaged projections over the P planes
       const dim3 grow(c.row_blocks(), nb), gcol(c.col_blocks(), nb * P);
@@ -696,7 +720,17 @@ hg_status gs_class(hg_plan* p, const SizeClass& c, const GsCall& g, cudaStream_t
         return s;
       continue;
     }
-    const dim3 grow(c.row_blocks(), nb), gcol(c.col_blocks(), nb);
+    // field layout: tiled in column strips when the row length allows (whole 128-byte lines for both
+    // passes), else row-major
+    const int ti = c.ck->cols == 4 ? 0 : (c.ck->cols == 8 ? 1 : 2);
+    const bool tiled = c.rk->init_t[ti] != nullptr && c.W % c.ck->cols == 0;
+    const void* k_init = tiled ? c.rk->init_t[ti] : c.rk->init;
+    const void* k_row[2] = {tiled ? c.rk->gs_t[ti][0] : c.rk->gs[0], tiled ? c.rk->gs_t[ti][1] : c.rk->gs[1]};
+    const void* k_col[2] = {tiled ? c.ck->gs_t[0] : c.ck->gs[0], tiled ? c.ck->gs_t[1] : c.ck->gs[1]};
+    const int rrows = tiled ? c.rk->rows_t[ti] : c.rk->rows;
+    const int rnt = tiled ? c.rk->nt_t[ti] : c.rk->nt;
+    const int rsm = tiled ? c.rk->smem_t[ti] : c.rk->smem;
+    const dim3 grow((c.H + rrows - 1) / rrows, nb), gcol(c.col_blocks(), nb);
     // prologue (writes h_0 out when there is no iteration)
     hg::PassArgs a0 = a;
     if (n_iter == 0)
@@ -705,7 +739,7 @@ hg_status gs_class(hg_plan* p, const SizeClass& c, const GsCall& g, cudaStream_t
         a0.phase_out[k] = phase_out ? phase_out[item] : nullptr;
         a0.level_out[k] = level_out ? level_out[item] : nullptr;
       }
-    if ((s = launch(p, K_ROW_INIT, c.rk->init, grow, c.rk->nt, c.rk->smem, a0, st)) != HG_OK) return s;
+    if ((s = launch(p, K_ROW_INIT, k_init, grow, rnt, rsm, a0, st)) != HG_OK) return s;
     hg::PassArgs ao = a;
     for (int k = 0; k < nb; ++k) {
       const int item = c.items[c0 + k];
@@ -714,16 +748,16 @@ hg_status gs_class(hg_plan* p, const SizeClass& c, const GsCall& g, cudaStream_t
     }
     for (int it = 0; it < n_iter; ++it) {
       a.iter = it;
-      if ((s = launch(p, K_COL_GS, c.ck->gs[1], gcol, c.ck->nt, c.ck->smem_gs, a, st)) != HG_OK) return s;
+      if ((s = launch(p, K_COL_GS, k_col[1], gcol, c.ck->nt, c.ck->smem_gs, a, st)) != HG_OK) return s;
       const bool last = it == n_iter - 1;
       hg::PassArgs ar = last ? ao : a;
       ar.finalize = nmse_out != nullptr;  // the row pass first adds up this column pass's NMSE
       ar.fin_iter = it;
-      if ((s = launch(p, K_ROW_GS, c.rk->gs[last], grow, c.rk->nt, c.rk->smem, ar, st)) != HG_OK) return s;
+      if ((s = launch(p, K_ROW_GS, k_row[last], grow, rnt, rsm, ar, st)) != HG_OK) return s;
     }
     a.iter = n_iter;
     a.fin_iter = n_iter;
-    if ((s = launch(p, K_COL_NMSE, c.ck->gs[0], gcol, c.ck->nt, c.ck->smem_gs, a, st)) != HG_OK) return s;
+    if ((s = launch(p, K_COL_NMSE, k_col[0], gcol, c.ck->nt, c.ck->smem_gs, a, st)) != HG_OK) return s;
     if (nmse_out && (s = launch(p, K_FINALIZE, (const void*)&hg::k_finalize<0>, dim3(1, nb), 32, 0, a, st)) != HG_OK)
       return s;
   }

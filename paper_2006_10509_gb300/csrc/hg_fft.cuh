@@ -276,6 +276,19 @@ HG_PLAN(1536, 16, 8, 4, 3)
 HG_PLAN(1920, 16, 8, 3, 5)
 #undef HG_PLAN
 
+// Whether rows of length N can be processed as interleaved groups of G butterflies (every stage's
+// butterfly count N / R a multiple of G) with the n ^ (G b) swizzle (N a multiple of 16).
+template <class L>
+struct RAll;
+template <int... Rs>
+struct RAll<RList<Rs...>> {
+  __host__ __device__ static constexpr bool divisible(int n, int g) { return ((n / Rs % g == 0) && ...); }
+};
+template <int N, int G>
+__host__ __device__ constexpr bool row_tileable() {
+  return G > 0 && N % 16 == 0 && N % G == 0 && RAll<typename PlanFor<N>::type>::divisible(N, G);
+}
+
 // Per-stage twiddle tables of length N.  A stage of radix R after Ns earlier points needs
 // w_{Ns R}^{r k} for r = 1..R-1, k = 0..Ns-1; its table stores them r-major, entry (r-1) Ns + k, so a
 // warp whose lanes hold consecutive k reads consecutive entries and the addresses of one butterfly
@@ -338,12 +351,16 @@ struct TwBlob {
 // B sequences of length N, NT threads.  COLS: a column strip (element (b, n) of the strip at global
 // row n, column col0 + b; in shared memory at n * B + b).  Otherwise a row tile (element (b, n) at
 // global row row0 + b, column n; in shared memory at b * N + n).
-template <int N_, int B_, int NT_, bool COLS_>
+// G_ > 1 (row tiles only): lanes interleave the B rows in groups of G_ consecutive butterflies, so that
+// a warp's global accesses of a column-strip-tiled field (G_ = tile width, B G_ = 16) cover whole
+// 128-byte lines; shared-memory rows are then swizzled (n ^ G_ b) to keep the exchange conflict-free.
+template <int N_, int B_, int NT_, bool COLS_, int G_ = 0>
 struct Geo {
   static constexpr int N = N_;
   static constexpr int B = B_;
   static constexpr int NT = NT_;
   static constexpr bool COLS = COLS_;
+  static constexpr bool ILV = !COLS_ && G_ > 1 && B_ > 1;
 
   template <int R>
   __host__ __device__ static constexpr int nbf() {
@@ -361,7 +378,7 @@ struct Geo {
   // Shared-memory slot of element (b, n), padded by one float2 per 16: the Stockham stores of a stage
   // with stride R (R = 4, 8, 16) land on distinct banks within each half-warp.
   __device__ __forceinline__ static int sidx(int b, int n) {
-    const int i = COLS ? n * B + b : b * N + n;
+    const int i = COLS ? n * B + b : (ILV ? b * N + (n ^ (G_ * b)) : b * N + n);
     return i + (i >> 4);
   }
   // float2 slots of the exchange buffer, rounded up to 128 bytes so that data placed after it is
@@ -375,6 +392,9 @@ struct Geo {
     if constexpr (COLS) {
       b = u % B;
       j = u / B;
+    } else if constexpr (ILV) {
+      b = (u / G_) % B;
+      j = (u / (G_ * B)) * G_ + u % G_;
     } else {
       j = u % (N / R);
       b = u / (N / R);
@@ -410,6 +430,18 @@ __device__ __forceinline__ void for_each_slot(int t, F&& f) {
   }
 }
 
+// As for_each_slot, but f(slot, b, j, r) (n = j + r N / R), for linear addressing in the caller.
+template <class G, int R, class F>
+__device__ __forceinline__ void for_each_slot_jr(int t, F&& f) {
+#pragma unroll
+  for (int i = 0; i < G::template bpt<R>(); ++i) {
+    int b, j;
+    if (!G::template bf<R>(t, i, b, j)) continue;
+#pragma unroll
+    for (int r = 0; r < R; ++r) f(i * R + r, b, j, r);
+  }
+}
+
 template <class G, int R, int NS, bool INV, int V>
 __device__ __forceinline__ void stage_compute(float2 (&v)[V], int t, const float2* __restrict__ tw) {
 #pragma unroll
@@ -431,26 +463,49 @@ __device__ __forceinline__ void stage_compute(float2 (&v)[V], int t, const float
   }
 }
 
+// Slot index steps of a stage: element n + r * STEP for r = 0..R-1.  When the step in the unpadded
+// index (STEP, times B in a column strip) is a multiple of 16, the padded (and swizzled) slot of
+// n + r * STEP is the slot of n plus r * 17 * step / 16, so one index is computed per butterfly.
+template <class G, int STEP>
+__host__ __device__ constexpr int padded_step() {
+  constexpr int raw = G::COLS ? STEP * G::B : STEP;
+  return raw % 16 == 0 ? raw / 16 * 17 : -1;
+}
+
 template <class G, int R, int NS, int V>
 __device__ __forceinline__ void stage_store(const float2 (&v)[V], float2* sm, int t) {
+  constexpr int PS = padded_step<G, NS>();
 #pragma unroll
   for (int i = 0; i < G::template bpt<R>(); ++i) {
     int b, j;
     if (!G::template bf<R>(t, i, b, j)) continue;
     const int base = (j / NS) * NS * R + (j % NS);
+    if constexpr (PS > 0) {
+      float2* q = sm + G::sidx(b, base);
 #pragma unroll
-    for (int r = 0; r < R; ++r) sm[G::sidx(b, base + r * NS)] = v[i * R + r];
+      for (int r = 0; r < R; ++r) q[r * PS] = v[i * R + r];
+    } else {
+#pragma unroll
+      for (int r = 0; r < R; ++r) sm[G::sidx(b, base + r * NS)] = v[i * R + r];
+    }
   }
 }
 
 template <class G, int R, int V>
 __device__ __forceinline__ void stage_load(float2 (&v)[V], const float2* sm, int t) {
+  constexpr int PS = padded_step<G, G::N / R>();
 #pragma unroll
   for (int i = 0; i < G::template bpt<R>(); ++i) {
     int b, j;
     if (!G::template bf<R>(t, i, b, j)) continue;
+    if constexpr (PS > 0) {
+      const float2* q = sm + G::sidx(b, j);
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[i * R + r] = sm[G::sidx(b, j + r * (G::N / R))];
+      for (int r = 0; r < R; ++r) v[i * R + r] = q[r * PS];
+    } else {
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[i * R + r] = sm[G::sidx(b, j + r * (G::N / R))];
+    }
   }
 }
 

@@ -40,12 +40,15 @@ __device__ __forceinline__ T* opaque(T* x) {
   return y;
 }
 
-// Row tile: ROWS rows of length W, about 16 values per thread.
-template <int W>
+// Row tile: ROWS rows of length W, about 16 values per thread.  TW > 0: the field is stored in
+// column-strip tiles of width TW (see fidx); the tile then holds 16 / TW rows whose lanes interleave
+// in groups of TW, so each warp access covers whole 128-byte lines of the tiled layout.
+template <int W, int TW = 0>
 struct RowCfg {
-  static constexpr int ROWS = hg_max(1, 4096 / W);
-  static constexpr int NT = hg_min(512, hg_max(32, round_up(ROWS * W / 16, 32)));
-  using G = Geo<W, ROWS, NT, false>;
+  static constexpr int ROWS = TW ? 16 / TW : hg_max(1, 4096 / W);
+  static constexpr int NT = hg_min(TW ? 1024 : 512, hg_max(32, round_up(ROWS * W / 16, 32)));
+  static constexpr int MINB = hg_min(8, hg_max(1, 1024 / NT));  // CTAs per SM at <= 64 registers
+  using G = Geo<W, ROWS, NT, false, (TW && ROWS > 1) ? TW : 0>;
   using Fwd = typename PlanFor<W>::type;
   using Inv = typename RRev<Fwd>::type;
   static constexpr int RE = RLast<Fwd>::value;   // radix of the global load/store stages
@@ -54,11 +57,11 @@ struct RowCfg {
   static constexpr int SMEM = G::SM_ELEMS * 8;
 };
 
-// Column strip: C columns of length H, about 16 values per thread.  Long columns use 4-column
-// strips (32-byte row segments, one L2 sector) so that two strips share an SM.
+// Column strip: C columns of length H, about 16 values per thread; 4-column strips for 4096-long
+// columns (an 8-column strip would not fit shared memory).
 template <int H>
 struct ColCfg {
-  static constexpr int C = H >= 2048 ? 4 : (H >= 640 ? 8 : 16);
+  static constexpr int C = H >= 4096 ? 4 : (H >= 640 ? 8 : 16);
   static constexpr int NT = hg_min(1024, hg_max(32, round_up(C * H / 16, 32)));
   using G = Geo<H, C, NT, true>;
   using Fwd = typename PlanFor<H>::type;
@@ -69,6 +72,17 @@ struct ColCfg {
   static constexpr int SMEM_T = SMEM + H * C * 4;  // + the strip's target values (GS passes)
   static constexpr int MINB = hg_max(1, 1024 / NT);  // CTAs per SM the register budget is cut for
 };
+
+// Global index of field element (row, n) of an [H][W] item: row-major (TW = 0), or column-strip
+// tiles of width TW ([W / TW][H][TW]), the layout in which a column pass reads its strip as one
+// contiguous block.
+template <int W, int TW>
+__device__ __forceinline__ size_t fidx(int row, int n, int H) {
+  if constexpr (TW == 0)
+    return (size_t)row * W + n;
+  else
+    return ((size_t)(n / TW) * H + row) * TW + (n % TW);
+}
 
 // ---------------------------------------------------------------- asynchronous copies
 
@@ -108,6 +122,13 @@ __device__ __forceinline__ void prefetch_strip(float* ts, const float* __restric
   cp_async_commit();
 }
 
+// Starts copying COUNT contiguous floats (COUNT % 4 == 0, both ends 16-byte aligned) into ts.
+template <int COUNT, int NT>
+__device__ __forceinline__ void prefetch_contig(float* ts, const float* __restrict__ src) {
+  for (int i = threadIdx.x; i < COUNT / 4; i += NT) cp_async16(ts + 4 * i, src + 4 * i);
+  cp_async_commit();
+}
+
 // ---------------------------------------------------------------- launch arguments
 
 // Per-launch argument block: up to kMaxBatch items of one size class.  Plan-owned buffers
@@ -135,6 +156,9 @@ struct PassArgs {
   int item_index[kMaxBatch];  // plan item index (nmse row, Philox key)
   int class_slot[kMaxBatch];  // slot in the class buffers
   const float* target[kMaxBatch];
+  const float* ttile;           // GS column passes: the targets re-laid out per column strip (slot P + p)
+                                // blocks of col_blocks strips, strip t holding [H][C] contiguous; or
+                                // nullptr to read the caller's [H][W] targets directly
   const float* phase_in[kMaxBatch];
   float* phase_out[kMaxBatch];
   uint8_t* level_out[kMaxBatch];
@@ -357,13 +381,50 @@ __global__ void __launch_bounds__(32) k_finalize(const __grid_constant__ PassArg
   if (MODE == 1 && threadIdx.x == 0 && a.loss) a.loss[(size_t)a.item_index[k] * (P + 1) + P] = (float)(m / P);
 }
 
+// ---------------------------------------------------------------- field I/O of row tiles
+
+// Global load / store of the radix-R first / last stage of a row tile.  In the tiled layout element
+// (row, j + r N/R) lies at fidx(row, j) + r (N/R) H (N/R is a multiple of the tile width), one
+// address per butterfly plus a stride.
+template <class K, int R, int TW>
+__device__ __forceinline__ void load_row_slots(float2 (&v)[K::V], const float2* __restrict__ f, int t, int row0,
+                                               int H) {
+  using G = typename K::G;
+  for_each_slot_jr<G, R>(t, [&](int s, int b, int j, int r) {
+    const int row = row0 + b;
+    float2 x = make_float2(0.f, 0.f);
+    if (row < H) {
+      if constexpr (TW == 0)
+        x = f[(size_t)row * G::N + j + r * (G::N / R)];
+      else
+        x = f[fidx<G::N, TW>(row, j, H) + (size_t)r * (G::N / R) * H];
+    }
+    v[s] = x;
+  });
+}
+
+template <class K, int R, int TW>
+__device__ __forceinline__ void store_row_slots(const float2 (&v)[K::V], float2* __restrict__ f, int t, int row0,
+                                                int H) {
+  using G = typename K::G;
+  for_each_slot_jr<G, R>(t, [&](int s, int b, int j, int r) {
+    const int row = row0 + b;
+    if (row < H) {
+      if constexpr (TW == 0)
+        f[(size_t)row * G::N + j + r * (G::N / R)] = v[s];
+      else
+        f[fidx<G::N, TW>(row, j, H) + (size_t)r * (G::N / R) * H] = v[s];
+    }
+  });
+}
+
 // ---------------------------------------------------------------- row passes
 
 // GS prologue: h0 = P_SLM(exp(i phi0)) (phi0 given, or drawn from the seed), times the chirp,
 // forward row FFTs -> field.  h0 is written out when phase_out / level_out are set.
-template <int W>
-__global__ void __launch_bounds__(RowCfg<W>::NT) k_row_init(const __grid_constant__ PassArgs a) {
-  using K = RowCfg<W>;
+template <int W, int TW>
+__global__ void __launch_bounds__(RowCfg<W, TW>::NT, RowCfg<W, TW>::MINB) k_row_init(const __grid_constant__ PassArgs a) {
+  using K = RowCfg<W, TW>;
   using G = typename K::G;
   extern __shared__ __align__(16) float2 sm[];
   const int t = threadIdx.x, k = blockIdx.y;
@@ -396,17 +457,14 @@ __global__ void __launch_bounds__(RowCfg<W>::NT) k_row_init(const __grid_constan
     v[s] = h;
   });
   FftRun<G, false, 1, typename K::Fwd>::run(v, sm, t, a.tw_row);
-  for_each_slot<G, RLast<typename K::Fwd>::value>(t, [&](int s, int b, int n) {
-    const int row = row0 + b;
-    if (row < H) f[(size_t)row * W + n] = v[s];
-  });
+  store_row_slots<K, RLast<typename K::Fwd>::value, TW>(v, f, t, row0, H);
 }
 
 // GS row pass: inverse row FFTs, conj chirp, SLM projection (optionally written out), chirp,
 // forward row FFTs.
-template <int W, bool OUT>
-__global__ void __launch_bounds__(RowCfg<W>::NT) k_row_gs(const __grid_constant__ PassArgs a) {
-  using K = RowCfg<W>;
+template <int W, bool OUT, int TW>
+__global__ void __launch_bounds__(RowCfg<W, TW>::NT, RowCfg<W, TW>::MINB) k_row_gs(const __grid_constant__ PassArgs a) {
+  using K = RowCfg<W, TW>;
   using G = typename K::G;
   extern __shared__ __align__(16) float2 sm[];
   const int t = threadIdx.x, k = blockIdx.y;
@@ -415,10 +473,7 @@ __global__ void __launch_bounds__(RowCfg<W>::NT) k_row_gs(const __grid_constant_
   const int H = a.H;
   float2* f = a.field + (size_t)a.class_slot[k] * H * W;
   float2 v[K::V];
-  for_each_slot<G, K::RE>(t, [&](int s, int b, int n) {
-    const int row = row0 + b;
-    v[s] = row < H ? f[(size_t)row * W + n] : make_float2(0.f, 0.f);
-  });
+  load_row_slots<K, K::RE, TW>(v, f, t, row0, H);
   FftRun<G, true, 1, typename K::Inv>::run(v, sm, t, a.tw_row);
   float* po = OUT ? a.phase_out[k] : nullptr;
   uint8_t* lo = OUT ? a.level_out[k] : nullptr;
@@ -441,10 +496,11 @@ __global__ void __launch_bounds__(RowCfg<W>::NT) k_row_gs(const __grid_constant_
     v[s] = row < H ? h : make_float2(0.f, 0.f);
   });
   FftRun<G, false, 1, typename K::Fwd>::run(v, sm, t, a.tw_row);
-  for_each_slot<G, K::RE>(t, [&](int s, int b, int n) {
-    const int row = row0 + b;
-    if (row < H) f[(size_t)row * W + n] = v[s];
-  });
+  // tiled: re-derive the (run-time stride) store addresses rather than keep the load's live
+  if (TW)
+    store_row_slots<K, K::RE, TW>(v, opaque(f), t, row0, opaque(H));
+  else
+    store_row_slots<K, K::RE, TW>(v, f, t, row0, H);
 }
 
 // Bare row FFTs (propagation): in (times the chirp when PRE) -> FFT -> out.
@@ -480,7 +536,7 @@ __global__ void __launch_bounds__(RowCfg<W>::NT) k_row_fft(const __grid_constant
 // GS column pass: forward column FFTs -> NMSE partials of I = |R|^2 against T = A^2 and
 // amplitude replacement R' = A R / |R| -> inverse column FFTs.  With REPLACE = false only the NMSE
 // is taken (last iteration) and the field is not written.
-template <int H, bool REPLACE>
+template <int H, bool REPLACE, bool TILED>
 __global__ void __launch_bounds__(ColCfg<H>::NT, ColCfg<H>::MINB) k_col_gs(const __grid_constant__ PassArgs a) {
   using K = ColCfg<H>;
   using G = typename K::G;
@@ -496,11 +552,19 @@ __global__ void __launch_bounds__(ColCfg<H>::NT, ColCfg<H>::MINB) k_col_gs(const
   // (A_s = A sqrt(HW / sum A^2)); the common sqrt(HW) is dropped.  One plane needs no scale.
   const float amp_scale = P > 1 ? (float)__ldcg(&a.stats[((size_t)slot * P + p) * 4 + 3]) : 1.f;
   float* ts = reinterpret_cast<float*>(sm + G::SM_ELEMS);  // the strip's target, [n][C]
-  prefetch_strip<H, K::C, K::NT>(ts, A, col0, W);
+  if (a.ttile)
+    prefetch_contig<H * K::C, K::NT>(ts, a.ttile + (((size_t)slot * P + p) * gridDim.x + blockIdx.x) * H * K::C);
+  else
+    prefetch_strip<H, K::C, K::NT>(ts, A, col0, W);
+  // tiled: this strip is one contiguous [H][C] block
+  float2* fs = TILED ? f + (size_t)blockIdx.x * H * K::C : f;
   float2 v[K::V];
   for_each_slot<G, K::RB>(t, [&](int s, int b, int n) {
     const int col = col0 + b;
-    v[s] = col < W ? f[n * W + col] : make_float2(0.f, 0.f);  // 32-bit offsets: H W < 2^31
+    if (TILED)
+      v[s] = fs[n * K::C + b];
+    else
+      v[s] = col < W ? f[n * W + col] : make_float2(0.f, 0.f);  // 32-bit offsets: H W < 2^31
   });
   FftRun<G, false, 1, typename K::Fwd>::run(v, sm, t, a.tw_col);
   cp_async_wait_all();
@@ -521,12 +585,17 @@ __global__ void __launch_bounds__(ColCfg<H>::NT, ColCfg<H>::MINB) k_col_gs(const
   });
   if (REPLACE) {
     FftRun<G, true, 1, typename K::Inv>::run(v, sm, t, a.tw_col);
-    const int Wo = opaque(W);
-    float2* fo = opaque(f);
-    for_each_slot<G, K::RB>(t, [&](int s, int b, int n) {
-      const int col = col0 + b;
-      if (col < Wo) fo[n * Wo + col] = v[s];
-    });
+    if (TILED) {
+      float2* fo = opaque(fs);
+      for_each_slot<G, K::RB>(t, [&](int s, int b, int n) { fo[n * K::C + b] = v[s]; });
+    } else {
+      const int Wo = opaque(W);
+      float2* fo = opaque(f);
+      for_each_slot<G, K::RB>(t, [&](int s, int b, int n) {
+        const int col = col0 + b;
+        if (col < Wo) fo[n * Wo + col] = v[s];
+      });
+    }
   }
   block_partials(s_it, s_ii, s_tt, a.partials + ((size_t)slot * P + p) * 3 * gridDim.x);
 }

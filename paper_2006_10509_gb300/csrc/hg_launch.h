@@ -17,8 +17,13 @@ struct RowKernels {
   int rows;      // rows per CTA
   int nt;        // threads per CTA
   int smem;      // dynamic shared memory bytes
-  const void* init;         // k_row_init
-  const void* gs[2];        // k_row_gs<OUT = false / true>
+  const void* init;         // k_row_init (row-major field)
+  const void* gs[2];        // k_row_gs<OUT = false / true> (row-major field)
+  // the same on a field tiled in column strips of width 4 / 8 / 16 (nullptr where the row length
+  // does not allow it); rows / threads / shared memory of those tiles
+  const void* init_t[3];
+  const void* gs_t[3][2];
+  int rows_t[3], nt_t[3], smem_t[3];
   const void* fft[2][2];    // k_row_fft<INV><PRE>
   const void* ospr[2];      // k_row_ospr<BITS = false / true>
   int smem_ospr;            // dynamic shared memory of k_row_ospr (field tile + bit decisions)
@@ -34,7 +39,8 @@ struct ColKernels {
   int nt;
   int smem;
   int smem_gs;              // dynamic shared memory of k_col_gs (exchange buffer + target strip)
-  const void* gs[2];        // k_col_gs<REPLACE = false / true>
+  const void* gs[2];        // k_col_gs<REPLACE = false / true> (row-major field)
+  const void* gs_t[2];      // the same on a field tiled in this strip width
   const void* fft[2][2];    // k_col_fft<INV><POST>
   const void* ospr[3];      // k_col_ospr: [0] start only, [1] finish + start, [2] finish only
   const void* gd[2];        // k_col_gd<BWD = false / true>

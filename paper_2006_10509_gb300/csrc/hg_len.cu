@@ -30,6 +30,28 @@ TwiddleLayout make_tw() {
   return l;
 }
 
+template <int N, int TW>
+void fill_tiled(RowKernels& r, int i) {
+  if constexpr (row_tileable<N, TW>()) {
+    using K = RowCfg<N, TW>;
+    r.init_t[i] = (const void*)&k_row_init<N, TW>;
+    r.gs_t[i][0] = (const void*)&k_row_gs<N, false, TW>;
+    r.gs_t[i][1] = (const void*)&k_row_gs<N, true, TW>;
+    r.rows_t[i] = K::ROWS;
+    r.nt_t[i] = K::NT;
+    r.smem_t[i] = K::SMEM;
+  }
+}
+
+template <int N, int TW>
+void set_tiled_attrs() {
+  if constexpr (row_tileable<N, TW>()) {
+    allow_smem(&k_row_init<N, TW>, RowCfg<N, TW>::SMEM);
+    allow_smem(&k_row_gs<N, false, TW>, RowCfg<N, TW>::SMEM);
+    allow_smem(&k_row_gs<N, true, TW>, RowCfg<N, TW>::SMEM);
+  }
+}
+
 template <int N>
 RowKernels make_row() {
   using K = RowCfg<N>;
@@ -37,9 +59,12 @@ RowKernels make_row() {
   r.rows = K::ROWS;
   r.nt = K::NT;
   r.smem = K::SMEM;
-  r.init = (const void*)&k_row_init<N>;
-  r.gs[0] = (const void*)&k_row_gs<N, false>;
-  r.gs[1] = (const void*)&k_row_gs<N, true>;
+  r.init = (const void*)&k_row_init<N, 0>;
+  r.gs[0] = (const void*)&k_row_gs<N, false, 0>;
+  r.gs[1] = (const void*)&k_row_gs<N, true, 0>;
+  fill_tiled<N, 4>(r, 0);
+  fill_tiled<N, 8>(r, 1);
+  fill_tiled<N, 16>(r, 2);
   r.fft[0][0] = (const void*)&k_row_fft<N, false, false>;
   r.fft[0][1] = (const void*)&k_row_fft<N, false, true>;
   r.fft[1][0] = (const void*)&k_row_fft<N, true, false>;
@@ -64,8 +89,10 @@ ColKernels make_col() {
   c.nt = K::NT;
   c.smem = K::SMEM;
   c.smem_gs = K::SMEM_T;
-  c.gs[0] = (const void*)&k_col_gs<N, false>;
-  c.gs[1] = (const void*)&k_col_gs<N, true>;
+  c.gs[0] = (const void*)&k_col_gs<N, false, false>;
+  c.gs[1] = (const void*)&k_col_gs<N, true, false>;
+  c.gs_t[0] = (const void*)&k_col_gs<N, false, true>;
+  c.gs_t[1] = (const void*)&k_col_gs<N, true, true>;
   c.fft[0][0] = (const void*)&k_col_fft<N, false, false>;
   c.fft[0][1] = (const void*)&k_col_fft<N, false, true>;
   c.fft[1][0] = (const void*)&k_col_fft<N, true, false>;
@@ -80,9 +107,12 @@ ColKernels make_col() {
 }
 
 void set_row_attrs(const RowKernels& r) {
-  allow_smem(&k_row_init<HG_LEN>, r.smem);
-  allow_smem(&k_row_gs<HG_LEN, false>, r.smem);
-  allow_smem(&k_row_gs<HG_LEN, true>, r.smem);
+  allow_smem(&k_row_init<HG_LEN, 0>, r.smem);
+  allow_smem(&k_row_gs<HG_LEN, false, 0>, r.smem);
+  allow_smem(&k_row_gs<HG_LEN, true, 0>, r.smem);
+  set_tiled_attrs<HG_LEN, 4>();
+  set_tiled_attrs<HG_LEN, 8>();
+  set_tiled_attrs<HG_LEN, 16>();
   allow_smem(&k_row_fft<HG_LEN, false, false>, r.smem);
   allow_smem(&k_row_fft<HG_LEN, false, true>, r.smem);
   allow_smem(&k_row_fft<HG_LEN, true, false>, r.smem);
@@ -97,8 +127,10 @@ void set_row_attrs(const RowKernels& r) {
 }
 
 void set_col_attrs(const ColKernels& c) {
-  allow_smem(&k_col_gs<HG_LEN, false>, c.smem_gs);
-  allow_smem(&k_col_gs<HG_LEN, true>, c.smem_gs);
+  allow_smem(&k_col_gs<HG_LEN, false, false>, c.smem_gs);
+  allow_smem(&k_col_gs<HG_LEN, true, false>, c.smem_gs);
+  allow_smem(&k_col_gs<HG_LEN, false, true>, c.smem_gs);
+  allow_smem(&k_col_gs<HG_LEN, true, true>, c.smem_gs);
   allow_smem(&k_col_fft<HG_LEN, false, false>, c.smem);
   allow_smem(&k_col_fft<HG_LEN, false, true>, c.smem);
   allow_smem(&k_col_fft<HG_LEN, true, false>, c.smem);
