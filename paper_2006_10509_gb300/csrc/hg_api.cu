@@ -722,7 +722,7 @@ hg_status gs_class(hg_plan* p, const SizeClass& c, const GsCall& g, cudaStream_t
     }
     // field layout: tiled in column strips when the row length allows (whole 128-byte lines for both
     // passes), else row-major
-    const int ti = c.ck->cols == 4 ? 0 : (c.ck->cols == 8 ? 1 : 2);
+    const int ti = c.ck->cols == 2 ? 0 : (c.ck->cols == 4 ? 1 : (c.ck->cols == 8 ? 2 : 3));
     const bool tiled = c.rk->init_t[ti] != nullptr && c.W % c.ck->cols == 0;
     const void* k_init = tiled ? c.rk->init_t[ti] : c.rk->init;
     const void* k_row[2] = {tiled ? c.rk->gs_t[ti][0] : c.rk->gs[0], tiled ? c.rk->gs_t[ti][1] : c.rk->gs[1]};

@@ -376,9 +376,12 @@ struct Geo {
   }
 
   // Shared-memory slot of element (b, n), padded by one float2 per 16: the Stockham stores of a stage
-  // with stride R (R = 4, 8, 16) land on distinct banks within each half-warp.
+  // with stride R (R = 4, 8, 16) land on distinct banks within each half-warp.  Interleaved row tiles
+  // also swizzle row b by (16 / B) b within each 16-element block, so that the B rows a warp touches
+  // at once start on different banks.
+  static constexpr int SWZ = B >= 16 ? 1 : 16 / B;
   __device__ __forceinline__ static int sidx(int b, int n) {
-    const int i = COLS ? n * B + b : (ILV ? b * N + (n ^ (G_ * b)) : b * N + n);
+    const int i = COLS ? n * B + b : (ILV ? b * N + (n ^ (SWZ * b)) : b * N + n);
     return i + (i >> 4);
   }
   // float2 slots of the exchange buffer, rounded up to 128 bytes so that data placed after it is

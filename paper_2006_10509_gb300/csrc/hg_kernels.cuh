@@ -41,11 +41,12 @@ __device__ __forceinline__ T* opaque(T* x) {
 }
 
 // Row tile: ROWS rows of length W, about 16 values per thread.  TW > 0: the field is stored in
-// column-strip tiles of width TW (see fidx); the tile then holds 16 / TW rows whose lanes interleave
-// in groups of TW, so each warp access covers whole 128-byte lines of the tiled layout.
+// column-strip tiles of width TW (see fidx); the tile holds 16 / TW rows (2 for TW = 2) whose lanes
+// interleave in groups of TW, so each warp access covers whole 128-byte lines of the tiled layout
+// (whole 32-byte sectors for TW = 2, where 8-row tiles of 1024 threads measured slower).
 template <int W, int TW = 0>
 struct RowCfg {
-  static constexpr int ROWS = TW ? 16 / TW : hg_max(1, 4096 / W);
+  static constexpr int ROWS = TW ? (TW >= 4 ? 16 / TW : 2) : hg_max(1, 4096 / W);
   static constexpr int NT = hg_min(TW ? 1024 : 512, hg_max(32, round_up(ROWS * W / 16, 32)));
   static constexpr int MINB = hg_min(8, hg_max(1, 1024 / NT));  // CTAs per SM at <= 64 registers
   using G = Geo<W, ROWS, NT, false, (TW && ROWS > 1) ? TW : 0>;
@@ -57,11 +58,13 @@ struct RowCfg {
   static constexpr int SMEM = G::SM_ELEMS * 8;
 };
 
-// Column strip: C columns of length H, about 16 values per thread; 4-column strips for 4096-long
-// columns (an 8-column strip would not fit shared memory).
+// Column strip: C columns of length H, about 16 values per thread.  Widths measured on GB300 (GS,
+// 100 iterations): 2-column strips (256 / 512 threads, several CTAs per SM, so barriers span few
+// warps and the last wave is short) beat 8-column ones by 7-11 % at 2048 and 4096 rows and 12 % at
+// 512; at 1024 rows 8-column strips are 8 % faster.
 template <int H>
 struct ColCfg {
-  static constexpr int C = H >= 4096 ? 4 : (H >= 640 ? 8 : 16);
+  static constexpr int C = H >= 2048 ? 2 : (H >= 640 ? 8 : (H >= 384 ? 2 : 16));
   static constexpr int NT = hg_min(1024, hg_max(32, round_up(C * H / 16, 32)));
   using G = Geo<H, C, NT, true>;
   using Fwd = typename PlanFor<H>::type;

@@ -19,11 +19,11 @@ struct RowKernels {
   int smem;      // dynamic shared memory bytes
   const void* init;         // k_row_init (row-major field)
   const void* gs[2];        // k_row_gs<OUT = false / true> (row-major field)
-  // the same on a field tiled in column strips of width 4 / 8 / 16 (nullptr where the row length
-  // does not allow it); rows / threads / shared memory of those tiles
-  const void* init_t[3];
-  const void* gs_t[3][2];
-  int rows_t[3], nt_t[3], smem_t[3];
+  // the same on a field tiled in column strips of width 2 / 4 / 8 / 16 (nullptr where the row
+  // length does not allow it); rows / threads / shared memory of those tiles
+  const void* init_t[4];
+  const void* gs_t[4][2];
+  int rows_t[4], nt_t[4], smem_t[4];
   const void* fft[2][2];    // k_row_fft<INV><PRE>
   const void* ospr[2];      // k_row_ospr<BITS = false / true>
   int smem_ospr;            // dynamic shared memory of k_row_ospr (field tile + bit decisions)

@@ -62,9 +62,10 @@ RowKernels make_row() {
   r.init = (const void*)&k_row_init<N, 0>;
   r.gs[0] = (const void*)&k_row_gs<N, false, 0>;
   r.gs[1] = (const void*)&k_row_gs<N, true, 0>;
-  fill_tiled<N, 4>(r, 0);
-  fill_tiled<N, 8>(r, 1);
-  fill_tiled<N, 16>(r, 2);
+  fill_tiled<N, 2>(r, 0);
+  fill_tiled<N, 4>(r, 1);
+  fill_tiled<N, 8>(r, 2);
+  fill_tiled<N, 16>(r, 3);
   r.fft[0][0] = (const void*)&k_row_fft<N, false, false>;
   r.fft[0][1] = (const void*)&k_row_fft<N, false, true>;
   r.fft[1][0] = (const void*)&k_row_fft<N, true, false>;
@@ -110,6 +111,7 @@ void set_row_attrs(const RowKernels& r) {
   allow_smem(&k_row_init<HG_LEN, 0>, r.smem);
   allow_smem(&k_row_gs<HG_LEN, false, 0>, r.smem);
   allow_smem(&k_row_gs<HG_LEN, true, 0>, r.smem);
+  set_tiled_attrs<HG_LEN, 2>();
   set_tiled_attrs<HG_LEN, 4>();
   set_tiled_attrs<HG_LEN, 8>();
   set_tiled_attrs<HG_LEN, 16>();
