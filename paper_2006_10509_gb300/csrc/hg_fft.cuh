@@ -24,8 +24,9 @@ namespace hg {
 
 // ---------------------------------------------------------------- complex helpers
 
-__device__ __forceinline__ float2 c_add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 c_sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// complex add / subtract as one packed FP32x2 instruction (sm_100+), same rounding as two scalar ones
+__device__ __forceinline__ float2 c_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 c_sub(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
 __device__ __forceinline__ float2 c_mul(float2 a, float2 b) {
   return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
@@ -83,11 +84,12 @@ __device__ __forceinline__ void dft2(float2& a, float2& b) {
 template <bool INV>
 __device__ __forceinline__ void dft4(float2& x0, float2& x1, float2& x2, float2& x3) {
   float2 a = c_add(x0, x2), b = c_sub(x0, x2);
-  float2 c = c_add(x1, x3), d = c_rot<INV>(c_sub(x1, x3));
+  float2 c = c_add(x1, x3), s = c_sub(x1, x3);
   x0 = c_add(a, c);
   x2 = c_sub(a, c);
-  x1 = c_add(b, d);
-  x3 = c_sub(b, d);
+  // b -+ i s (forward) / b +- i s (inverse) in scalar form: a packed form would need a swapped pair
+  x1 = INV ? make_float2(b.x - s.y, b.y + s.x) : make_float2(b.x + s.y, b.y - s.x);
+  x3 = INV ? make_float2(b.x + s.y, b.y - s.x) : make_float2(b.x - s.y, b.y + s.x);
 }
 
 template <bool INV>
@@ -381,8 +383,18 @@ struct Geo {
   // also swizzle row b by (16 / B) b within each 16-element block, so that the B rows a warp touches
   // at once start on different banks.
   static constexpr int SWZ = B >= 16 ? 1 : 16 / B;
+  // ALT: the layout of the exchange after a radix-8 first stage (each thread stores 8 consecutive
+  // values).  For 2-row tiles the 8 b swizzle leaves that exchange 2-way conflicted and 12 b makes
+  // it conflict-free (measured: row pass 31.2 -> 29.9 us at 2048).  Column strips keep their layout
+  // (a row-style one removes the conflicts there too, but measured no faster).
+  static constexpr bool ROW_ALT = B == 2 && !COLS;
+  template <bool ALT = false>
   __device__ __forceinline__ static int sidx(int b, int n) {
-    const int i = COLS ? n * B + b : (ILV ? b * N + (n ^ (SWZ * b)) : b * N + n);
+    int i;
+    if constexpr (ALT && ROW_ALT)
+      i = ILV ? b * N + (n ^ (12 * b)) : b * N + n;
+    else
+      i = COLS ? n * B + b : (ILV ? b * N + (n ^ (SWZ * b)) : b * N + n);
     return i + (i >> 4);
   }
   // float2 slots of the exchange buffer, rounded up to 128 bytes so that data placed after it is
@@ -474,45 +486,52 @@ __device__ __forceinline__ void stage_compute(float2 (&v)[V], int t, const float
 // Slot index steps of a stage: element n + r * STEP for r = 0..R-1.  When the step in the unpadded
 // index (STEP, times B in a column strip) is a multiple of 16, the padded (and swizzled) slot of
 // n + r * STEP is the slot of n plus r * 17 * step / 16, so one index is computed per butterfly.
-template <class G, int STEP>
+template <class G, int STEP, bool ALT = false>
 __host__ __device__ constexpr int padded_step() {
   constexpr int raw = G::COLS ? STEP * G::B : STEP;
   return raw % 16 == 0 ? raw / 16 * 17 : -1;
 }
 
+// The exchange after stage (R, NS) uses the ALT layout when that stage is a radix-8 first stage.
+template <int R, int NS>
+__host__ __device__ constexpr bool alt_exchange() {
+  return R == 8 && NS == 1;
+}
+
 template <class G, int R, int NS, int V>
 __device__ __forceinline__ void stage_store(const float2 (&v)[V], float2* sm, int t) {
-  constexpr int PS = padded_step<G, NS>();
+  constexpr bool ALT = alt_exchange<R, NS>();
+  constexpr int PS = padded_step<G, NS, ALT>();
 #pragma unroll
   for (int i = 0; i < G::template bpt<R>(); ++i) {
     int b, j;
     if (!G::template bf<R>(t, i, b, j)) continue;
     const int base = (j / NS) * NS * R + (j % NS);
     if constexpr (PS > 0) {
-      float2* q = sm + G::sidx(b, base);
+      float2* q = sm + G::template sidx<ALT>(b, base);
 #pragma unroll
       for (int r = 0; r < R; ++r) q[r * PS] = v[i * R + r];
     } else {
 #pragma unroll
-      for (int r = 0; r < R; ++r) sm[G::sidx(b, base + r * NS)] = v[i * R + r];
+      for (int r = 0; r < R; ++r) sm[G::template sidx<ALT>(b, base + r * NS)] = v[i * R + r];
     }
   }
 }
 
-template <class G, int R, int V>
+template <class G, int R, bool ALT, int V>
 __device__ __forceinline__ void stage_load(float2 (&v)[V], const float2* sm, int t) {
-  constexpr int PS = padded_step<G, G::N / R>();
+  constexpr int PS = padded_step<G, G::N / R, ALT>();
 #pragma unroll
   for (int i = 0; i < G::template bpt<R>(); ++i) {
     int b, j;
     if (!G::template bf<R>(t, i, b, j)) continue;
     if constexpr (PS > 0) {
-      const float2* q = sm + G::sidx(b, j);
+      const float2* q = sm + G::template sidx<ALT>(b, j);
 #pragma unroll
       for (int r = 0; r < R; ++r) v[i * R + r] = q[r * PS];
     } else {
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[i * R + r] = sm[G::sidx(b, j + r * (G::N / R))];
+      for (int r = 0; r < R; ++r) v[i * R + r] = sm[G::template sidx<ALT>(b, j + r * (G::N / R))];
     }
   }
 }
@@ -530,7 +549,7 @@ struct FftRun<G, INV, NS, RList<R, Rs...>> {
       __syncthreads();  // everyone is done reading sm from the previous exchange
       stage_store<G, R, NS>(v, sm, t);
       __syncthreads();
-      stage_load<G, RFirst<RList<Rs...>>::value>(v, sm, t);
+      stage_load<G, RFirst<RList<Rs...>>::value, alt_exchange<R, NS>()>(v, sm, t);
       FftRun<G, INV, NS * R, RList<Rs...>>::run(v, sm, t, tw);
     }
   }

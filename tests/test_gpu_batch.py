@@ -12,7 +12,7 @@ import synth
 from oracle import gs as ogs
 from tests.helpers import check_nmse, cuda_device
 
-SIZES = [(64, 64), (128, 256), (64, 64), (256, 128), (864, 1536), (128, 256), (512, 512)] + [(16, 16)] * 40
+SIZES = [(64, 64), (128, 256), (64, 64), (256, 128), (864, 1536), (128, 256), (512, 512), (512, 512)] + [(16, 16)] * 40
 
 
 def _batch_inputs():
@@ -50,7 +50,7 @@ def test_batch_matches_single_item_plans_and_oracle():
     n_iter, levels = 6, 4
     (outs,), lat, _ = _run_plan(hg, dev, SIZES, targets, phases, n_iter, levels)
     lv_b, nm_b = outs
-    for i in [0, 1, 3, 4, 6, 7, 46]:
+    for i in [0, 1, 3, 4, 6, 7, 8, 47]:
         (single,), _, _ = _run_plan(hg, dev, [SIZES[i]], [targets[i]], [phases[i]], n_iter, levels)
         assert np.array_equal(single[0][0], lv_b[i]), i
         assert np.array_equal(single[1][0], nm_b[i]), i

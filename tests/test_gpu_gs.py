@@ -52,6 +52,9 @@ CASES = [
     (1024, 1024, 8, 0.1),
     (2048, 2048, 4, None),
     (2048, 2048, 0, None),
+    # 2-column tiles: Fresnel chirps on square and non-square items
+    (512, 512, 0, 0.08),
+    (2048, 512, 4, 0.1),
 ]
 
 
@@ -158,3 +161,4 @@ def test_gs_is_deterministic():
     r1 = _run(hg, dev, a, 5, 4, None, seed=3)
     r2 = _run(hg, dev, a, 5, 4, None, seed=3)
     assert np.array_equal(r1[1], r2[1]) and np.array_equal(r1[2], r2[2])
+
