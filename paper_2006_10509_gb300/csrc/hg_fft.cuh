@@ -20,6 +20,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace hg {
 
 // ---------------------------------------------------------------- complex helpers
@@ -174,6 +176,95 @@ __device__ __forceinline__ void dft16(float2* v) {
   for (int i = 0; i < 16; ++i) v[i] = t[i];
 }
 
+// cos and sin of 2 pi m / r, evaluated at compile time in double: the angle is brought to
+// [-pi, pi] and summed as a Taylor series (30 terms: truncation far below double rounding there).
+__host__ __device__ constexpr double turn_angle(int m, int r) {
+  const int k = ((m % r) + r) % r;
+  const double pi = 3.14159265358979323846264338327950288;
+  return 2.0 * k > r ? 2.0 * pi * (double)(k - r) / r : 2.0 * pi * (double)k / r;
+}
+__host__ __device__ constexpr double cos_turn(int m, int r) {
+  const double x = turn_angle(m, r);
+  double term = 1.0, sum = 1.0;
+  for (int i = 1; i <= 30; ++i) {
+    term *= -x * x / ((2.0 * i - 1.0) * (2.0 * i));
+    sum += term;
+  }
+  return sum;
+}
+__host__ __device__ constexpr double sin_turn(int m, int r) {
+  const double x = turn_angle(m, r);
+  double term = x, sum = x;
+  for (int i = 1; i <= 30; ++i) {
+    term *= -x * x / ((2.0 * i) * (2.0 * i + 1.0));
+    sum += term;
+  }
+  return sum;
+}
+
+// a * w_R^M, w_R = exp(-+ 2 pi i / R) (forward / inverse), M a compile-time constant
+template <int R, int M, bool INV>
+__device__ __forceinline__ float2 c_wt(float2 a) {
+  constexpr int m = ((M % R) + R) % R;
+  if constexpr (m == 0) {
+    return a;
+  } else if constexpr (4 * m == R) {
+    return c_rot<INV>(a);
+  } else if constexpr (2 * m == R) {
+    return make_float2(-a.x, -a.y);
+  } else if constexpr (4 * m == 3 * R) {
+    return c_rot<!INV>(a);
+  } else {
+    constexpr float c = (float)cos_turn(m, R);
+    constexpr float sn = (float)sin_turn(m, R);
+    constexpr float s = INV ? sn : -sn;
+    return make_float2(fmaf(a.x, c, -a.y * s), fmaf(a.x, s, a.y * c));
+  }
+}
+
+template <int R, bool INV>
+__device__ __forceinline__ void dft(float2* v);
+
+// Compile-time loop: f(std::integral_constant<int, I>) for I = B .. E-1.
+template <int B, int E, class F>
+__device__ __forceinline__ void static_for(F&& f) {
+  if constexpr (B < E) {
+    f(std::integral_constant<int, B>{});
+    static_for<B + 1, E>(f);
+  }
+}
+
+// R = P Q point DFT (Cooley-Tukey, one level): with n = Q n1 + n2 and k = k1 + P k2,
+// X[k] = sum_n2 w_R^(n2 k1) w_Q^(n2 k2) sum_n1 x[Q n1 + n2] w_P^(n1 k1): Q P-point DFTs, twiddles,
+// P Q-point DFTs, natural order out.
+template <int P, int Q, bool INV>
+__device__ __forceinline__ void dft_pq(float2* v) {
+  constexpr int R = P * Q;
+  static_for<0, Q>([&](auto n2c) {
+    constexpr int n2 = decltype(n2c)::value;
+    float2 t[P];
+#pragma unroll
+    for (int n1 = 0; n1 < P; ++n1) t[n1] = v[Q * n1 + n2];
+    dft<P, INV>(t);
+    static_for<0, P>([&](auto k1c) {
+      constexpr int k1 = decltype(k1c)::value;
+      v[Q * k1 + n2] = c_wt<R, n2 * k1, INV>(t[k1]);
+    });
+  });
+  float2 o[R];
+#pragma unroll
+  for (int k1 = 0; k1 < P; ++k1) {
+    float2 u[Q];
+#pragma unroll
+    for (int n2 = 0; n2 < Q; ++n2) u[n2] = v[Q * k1 + n2];
+    dft<Q, INV>(u);
+#pragma unroll
+    for (int k2 = 0; k2 < Q; ++k2) o[k1 + P * k2] = u[k2];
+  }
+#pragma unroll
+  for (int i = 0; i < R; ++i) v[i] = o[i];
+}
+
 template <int R, bool INV>
 __device__ __forceinline__ void dft(float2* v) {
   if constexpr (R == 2) {
@@ -188,6 +279,16 @@ __device__ __forceinline__ void dft(float2* v) {
     dft8<INV>(v);
   } else if constexpr (R == 16) {
     dft16<INV>(v);
+  } else if constexpr (R == 6) {
+    dft_pq<2, 3, INV>(v);
+  } else if constexpr (R == 9) {
+    dft_pq<3, 3, INV>(v);
+  } else if constexpr (R == 10) {
+    dft_pq<2, 5, INV>(v);
+  } else if constexpr (R == 12) {
+    dft_pq<4, 3, INV>(v);
+  } else if constexpr (R == 15) {
+    dft_pq<3, 5, INV>(v);
   } else {
     static_assert(R == 2, "unsupported radix");
   }
@@ -267,16 +368,41 @@ HG_PLAN(512, 8, 8, 8)
 HG_PLAN(1024, 16, 8, 8)
 HG_PLAN(2048, 16, 16, 8)
 HG_PLAN(4096, 16, 16, 16)
-HG_PLAN(12, 4, 3)
-HG_PLAN(15, 5, 3)
-HG_PLAN(30, 2, 3, 5)
-HG_PLAN(60, 4, 3, 5)
-HG_PLAN(120, 8, 3, 5)
-HG_PLAN(864, 8, 4, 3, 3, 3)
-HG_PLAN(1080, 8, 3, 3, 3, 5)
-HG_PLAN(1536, 16, 8, 4, 3)
-HG_PLAN(1920, 16, 8, 3, 5)
+// lengths with factors 3 and 5 use the composite radices 6, 9, 12, 15 so that no plan needs more
+// than three stages (two shared-memory exchanges)
+HG_PLAN(12, 12)
+HG_PLAN(15, 15)
+HG_PLAN(30, 2, 15)
+HG_PLAN(60, 4, 15)
+HG_PLAN(120, 8, 15)
+HG_PLAN(864, 16, 6, 9)
+HG_PLAN(1080, 8, 9, 15)
+HG_PLAN(1536, 16, 16, 6)
+HG_PLAN(1920, 16, 8, 15)
 #undef HG_PLAN
+
+// Values a thread holds in the widest stage of plan L when NT threads transform B sequences of
+// length N (each stage: ceil(B N / R / NT) butterflies of R values).
+template <class L>
+struct RValues;
+template <int... Rs>
+struct RValues<RList<Rs...>> {
+  __host__ __device__ static constexpr int max_values(int n, int b, int nt) {
+    int v = 0;
+    ((v = v > (b * n / Rs + nt - 1) / nt * Rs ? v : (b * n / Rs + nt - 1) / nt * Rs), ...);
+    return v;
+  }
+};
+// Fewest threads (a multiple of 32, at most cap) with which no thread holds more than vmax values;
+// cap when none is that small.
+template <class L>
+__host__ __device__ constexpr int pick_threads(int n, int b, int vmax, int cap) {
+  for (int nt = 32; nt < cap; nt += 32)
+    if (RValues<L>::max_values(n, b, nt) <= vmax) return nt;
+  return cap;
+}
+// value budget per thread: 16 for power-of-two lengths (radix-16 stages), 18 with factors 3 and 5
+__host__ __device__ constexpr int value_budget(int n) { return (n & (n - 1)) == 0 ? 16 : 18; }
 
 // Whether rows of length N can be processed as interleaved groups of G butterflies (every stage's
 // butterfly count N / R a multiple of G) with the n ^ (G b) swizzle (N a multiple of 16).

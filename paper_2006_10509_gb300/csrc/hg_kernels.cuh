@@ -47,7 +47,8 @@ __device__ __forceinline__ T* opaque(T* x) {
 template <int W, int TW = 0>
 struct RowCfg {
   static constexpr int ROWS = TW ? (TW >= 4 ? 16 / TW : 2) : hg_max(1, 4096 / W);
-  static constexpr int NT = hg_min(TW ? 1024 : 512, hg_max(32, round_up(ROWS * W / 16, 32)));
+  static constexpr int NT =
+      pick_threads<typename PlanFor<W>::type>(W, ROWS, value_budget(W), TW ? 1024 : 512);
   static constexpr int MINB = hg_min(8, hg_max(1, 1024 / NT));  // CTAs per SM at <= 64 registers
   using G = Geo<W, ROWS, NT, false, (TW && ROWS > 1) ? TW : 0>;
   using Fwd = typename PlanFor<W>::type;
@@ -61,11 +62,12 @@ struct RowCfg {
 // Column strip: C columns of length H, about 16 values per thread.  Widths measured on GB300 (GS,
 // 100 iterations): 2-column strips (256 / 512 threads, several CTAs per SM, so barriers span few
 // warps and the last wave is short) beat 8-column ones by 7-11 % at 2048 and 4096 rows and 12 % at
-// 512; at 1024 rows 8-column strips are 8 % faster.
+// 512; at 1024 rows 8-column strips are 8 % faster; at 1080 rows (1080 x 1920) 4-column strips are
+// 14 % faster than 8 and 20 % faster than 2; 864 rows are indifferent.
 template <int H>
 struct ColCfg {
-  static constexpr int C = H >= 2048 ? 2 : (H >= 640 ? 8 : (H >= 384 ? 2 : 16));
-  static constexpr int NT = hg_min(1024, hg_max(32, round_up(C * H / 16, 32)));
+  static constexpr int C = H >= 2048 ? 2 : (H == 1080 ? 4 : (H >= 640 ? 8 : (H >= 384 ? 2 : 16)));
+  static constexpr int NT = pick_threads<typename PlanFor<H>::type>(H, C, value_budget(H), 1024);
   using G = Geo<H, C, NT, true>;
   using Fwd = typename PlanFor<H>::type;
   using Inv = typename RRev<Fwd>::type;
