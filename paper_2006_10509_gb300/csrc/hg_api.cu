@@ -877,8 +877,9 @@ hg_status hg_ospr_run(hg_plan* p, const float* const* target_amp, int32_t n_subf
   }
   if (nmse_out && (s = check_ptr(p, nmse_out, (size_t)p->n_items * n_subframes * 4, 4, "nmse_out", 0)) != HG_OK)
     return s;
-  for (SizeClass& c : p->classes)
-    if (!c.acc && (s = p->alloc(&c.acc, c.items.size() * (size_t)c.H * c.W, "OSPR intensity buffer")) != HG_OK)
+  for (SizeClass& c : p->classes)  // [slot][strip][H][C]
+    if (!c.acc && (s = p->alloc(&c.acc, c.items.size() * (size_t)c.col_blocks() * c.H * c.ck->cols,
+                                "OSPR intensity buffer")) != HG_OK)
       return s;
 
   std::vector<uintptr_t> key{2, (uintptr_t)n_subframes, (uintptr_t)n_iter, (uintptr_t)seed, (uintptr_t)nmse_out};
@@ -911,8 +912,14 @@ hg_status hg_ospr_run(hg_plan* p, const float* const* target_amp, int32_t n_subf
         a.nmse = nmse_out;
         const dim3 grow(c.row_blocks(), nb), gcol(c.col_blocks(), nb);
         const int rs = c.rk->smem_ospr;
+        // targets re-laid out per column strip (read by every column pass of the run)
+        if ((s = launch(p, K_TILE_TARGET, (const void*)&k_tile_target, gcol, 256, 0, a, st, c.ck->cols, c.ttile)) !=
+            HG_OK)
+          return s;
+        a.ttile = c.ttile;
+        ag.ttile = c.ttile;
         a.iter = 0;
-        if ((s = launch(p, K_COL_OSPR, c.ck->ospr[0], gcol, c.ck->nt, c.ck->smem, a, st)) != HG_OK) return s;
+        if ((s = launch(p, K_COL_OSPR, c.ck->ospr[0], gcol, c.ck->nt, c.ck->smem_gs, a, st)) != HG_OK) return s;
         for (int sf = 0; sf < n_subframes; ++sf) {
           a.iter = sf;
           hg::PassArgs ar = a;  // the first row pass of subframe sf adds up NMSE[sf - 1]
@@ -927,7 +934,8 @@ hg_status hg_ospr_run(hg_plan* p, const float* const* target_amp, int32_t n_subf
           a.iter = sf + 1;
           a.acc_read = sf > 0;
           const int variant = sf + 1 < n_subframes ? 1 : 2;
-          if ((s = launch(p, K_COL_OSPR, c.ck->ospr[variant], gcol, c.ck->nt, c.ck->smem, a, st)) != HG_OK) return s;
+          if ((s = launch(p, K_COL_OSPR, c.ck->ospr[variant], gcol, c.ck->nt, c.ck->smem_gs, a, st)) != HG_OK)
+            return s;
         }
         a.fin_iter = n_subframes - 1;
         if (nmse_out && (s = launch(p, K_FINALIZE, (const void*)&hg::k_finalize<0>, dim3(1, nb), 32, 0, a, st)) != HG_OK)

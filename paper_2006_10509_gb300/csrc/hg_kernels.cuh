@@ -654,6 +654,8 @@ __device__ __forceinline__ float2 random_field(uint32_t p, int s, uint64_t seed,
 
 // FINISH: the field holds rowFFT(h_{s-1} c); accumulate its replay intensity (ACC_READ: add to the
 // stored sum, else start it) and write NMSE[s-1].  START: build subframe s and inverse-transform it.
+// The strip's target comes from the tiled copy (a.ttile, prefetched into shared memory) and the
+// accumulated intensity is kept per strip ([strip][H][C], a.acc), so both stream contiguously.
 template <int H, bool FINISH, bool START>
 __global__ void __launch_bounds__(ColCfg<H>::NT, ColCfg<H>::MINB) k_col_ospr(const __grid_constant__ PassArgs a) {
   using K = ColCfg<H>;
@@ -664,8 +666,10 @@ __global__ void __launch_bounds__(ColCfg<H>::NT, ColCfg<H>::MINB) k_col_ospr(con
   const int W = a.W;
   const int slot = a.class_slot[k];
   float2* f = a.field + (size_t)slot * H * W;
-  float* acc = a.acc + (size_t)slot * H * W;
-  const float* A = a.target[k];
+  const size_t strip = ((size_t)slot * gridDim.x + blockIdx.x) * H * K::C;
+  float* acc = a.acc + strip;
+  float* ts = reinterpret_cast<float*>(sm + G::SM_ELEMS);  // the strip's target, [n][C]
+  prefetch_contig<H * K::C, K::NT>(ts, a.ttile + strip);
   float2 v[K::V];
   float s_it = 0.f, s_ii = 0.f, s_tt = 0.f;
   if (FINISH) {
@@ -674,15 +678,17 @@ __global__ void __launch_bounds__(ColCfg<H>::NT, ColCfg<H>::MINB) k_col_ospr(con
       v[s] = col < W ? f[(size_t)n * W + col] : make_float2(0.f, 0.f);
     });
     FftRun<G, false, 1, typename K::Fwd>::run(v, sm, t, a.tw_col);
+    cp_async_wait_all();
+    __syncthreads();  // the target strip has landed
     for_each_slot<G, RLast<typename K::Fwd>::value>(t, [&](int s, int b, int n) {
       const int col = col0 + b;
       if (col < W) {
-        const size_t p = (size_t)n * W + col;
+        const int p = n * K::C + b;
         const float2 r = v[s];
         float i2 = fmaf(r.x, r.x, r.y * r.y);
         if (a.acc_read) i2 += acc[p];
         acc[p] = i2;
-        const float amp = __ldg(&A[p]);
+        const float amp = ts[p];
         const float tt = amp * amp;
         s_it = fmaf(i2, tt, s_it);
         s_ii = fmaf(i2, i2, s_ii);
@@ -691,13 +697,17 @@ __global__ void __launch_bounds__(ColCfg<H>::NT, ColCfg<H>::MINB) k_col_ospr(con
     });
   }
   if (START) {
-    if (FINISH) __syncthreads();  // the forward transform's last exchange is done with sm
+    // FINISH: its barrier above already saw the target land and the last exchange finish
+    if (!FINISH) {
+      cp_async_wait_all();
+      __syncthreads();
+    }
     for_each_slot<G, RFirst<typename K::Inv>::value>(t, [&](int s, int b, int n) {
       const int col = col0 + b;
       float2 e = make_float2(0.f, 0.f);
       if (col < W) {
-        const uint32_t p = (uint32_t)((size_t)n * W + col);
-        e = ospr::random_field(p, a.iter, a.seed, a.item_index[k], __ldg(&A[p]));
+        const uint32_t p = (uint32_t)((size_t)n * W + col);  // Philox counter: the pixel index
+        e = ospr::random_field(p, a.iter, a.seed, a.item_index[k], ts[n * K::C + b]);
       }
       v[s] = e;
     });

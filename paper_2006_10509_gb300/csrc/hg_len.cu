@@ -137,9 +137,9 @@ void set_col_attrs(const ColKernels& c) {
   allow_smem(&k_col_fft<HG_LEN, false, true>, c.smem);
   allow_smem(&k_col_fft<HG_LEN, true, false>, c.smem);
   allow_smem(&k_col_fft<HG_LEN, true, true>, c.smem);
-  allow_smem(&k_col_ospr<HG_LEN, false, true>, c.smem);
-  allow_smem(&k_col_ospr<HG_LEN, true, true>, c.smem);
-  allow_smem(&k_col_ospr<HG_LEN, true, false>, c.smem);
+  allow_smem(&k_col_ospr<HG_LEN, false, true>, c.smem_gs);
+  allow_smem(&k_col_ospr<HG_LEN, true, true>, c.smem_gs);
+  allow_smem(&k_col_ospr<HG_LEN, true, false>, c.smem_gs);
   allow_smem(&k_col_gd<HG_LEN, false>, c.smem);
   allow_smem(&k_col_gd<HG_LEN, true>, c.smem);
 }
