@@ -114,8 +114,17 @@ struct SizeClass {
   double* stats = nullptr;       // [slot][plane][4] gradient-descent loss statistics
   std::vector<float2*> cx, cy;   // per plane (Fresnel)
   int row_blocks() const { return (H + rk->rows - 1) / rk->rows; }
-  int col_blocks() const { return (W + ck->cols - 1) / ck->cols; }
+  int col_blocks() const { return (W + ck->cols - 1) / ck->cols; }    // strips on a row-major field
+  int col_blocks_t() const { return (W + ck->tile - 1) / ck->tile; }  // strips of the tiled GS field
+  // sizes covering either strip width: partial sums per strip, strips x H x width target copies
+  size_t max_strips() const { return (size_t)std::max(col_blocks(), col_blocks_t()); }
+  size_t max_strip_cols() const {
+    return std::max((size_t)col_blocks() * ck->cols, (size_t)col_blocks_t() * ck->tile);
+  }
 };
+
+// index of a column-strip tile width (2 / 4 / 8 / 16) in RowKernels' tiled tables
+int tile_index(int cols) { return cols == 2 ? 0 : (cols == 4 ? 1 : (cols == 8 ? 2 : 3)); }
 
 struct DeviceGuard {
   int prev = -1;
@@ -524,9 +533,9 @@ hg_status hg_plan_create(const hg_plan_desc* d, hg_plan** out) {
     c.ck->set_attrs();
     const size_t n = c.items.size() * (size_t)p->P;
     if ((s = p->alloc(&c.field, n * c.H * c.W, "field workspace")) != HG_OK) return bail(s);
-    if ((s = p->alloc(&c.partials, n * 3 * c.col_blocks(), "reduction scratch")) != HG_OK) return bail(s);
+    if ((s = p->alloc(&c.partials, n * 3 * c.max_strips(), "reduction scratch")) != HG_OK) return bail(s);
     if ((s = p->alloc(&c.stats, n * 4, "loss statistics")) != HG_OK) return bail(s);
-    if ((s = p->alloc(&c.ttile, n * c.col_blocks() * (size_t)c.H * c.ck->cols, "target tiles")) != HG_OK)
+    if ((s = p->alloc(&c.ttile, n * c.max_strip_cols() * c.H, "target tiles")) != HG_OK)
       return bail(s);
     if (cudaMemset(c.stats, 0, n * 4 * sizeof(double)) != cudaSuccess) return bail(cuda_fail(cudaGetLastError(), "memset"));
     for (int pl = 0; pl < p->P; ++pl) {
@@ -682,9 +691,16 @@ hg_status gs_class(hg_plan* p, const SizeClass& c, const GsCall& g, cudaStream_t
       for (int q = 0; q < P; ++q) a.target[k * P + q] = target_amp[item * P + q];
       a.phase_in[k] = init_phase ? init_phase[item] : nullptr;
     }
+    // field layout: single-plane runs tile the field in column strips when the row length allows
+    // (contiguous strips for the column pass), else row-major
+    const int ti = tile_index(c.ck->tile);
+    const bool tiled = P == 1 && c.rk->init_t[ti] != nullptr && c.W % c.ck->tile == 0;
+    const int strip = tiled ? c.ck->tile : c.ck->cols;
+    const int strips = tiled ? c.col_blocks_t() : c.col_blocks();
+    a.col_blocks = strips;
     // targets re-laid out per column strip once per run (read by every column pass of the run)
-    if ((s = launch(p, K_TILE_TARGET, (const void*)&k_tile_target, dim3(c.col_blocks(), nb * P), 256, 0, a, st,
-                    c.ck->cols, c.ttile)) != HG_OK)
+    if ((s = launch(p, K_TILE_TARGET, (const void*)&k_tile_target, dim3(strips, nb * P), 256, 0, a, st, strip,
+                    c.ttile)) != HG_OK)
       return s;
     a.ttile = c.ttile;
     if (P > 1) {
@@ -720,17 +736,15 @@ hg_status gs_class(hg_plan* p, const SizeClass& c, const GsCall& g, cudaStream_t
         return s;
       continue;
     }
-    // field layout: tiled in column strips when the row length allows (whole 128-byte lines for both
-    // passes), else row-major
-    const int ti = c.ck->cols == 2 ? 0 : (c.ck->cols == 4 ? 1 : (c.ck->cols == 8 ? 2 : 3));
-    const bool tiled = c.rk->init_t[ti] != nullptr && c.W % c.ck->cols == 0;
     const void* k_init = tiled ? c.rk->init_t[ti] : c.rk->init;
     const void* k_row[2] = {tiled ? c.rk->gs_t[ti][0] : c.rk->gs[0], tiled ? c.rk->gs_t[ti][1] : c.rk->gs[1]};
     const void* k_col[2] = {tiled ? c.ck->gs_t[0] : c.ck->gs[0], tiled ? c.ck->gs_t[1] : c.ck->gs[1]};
     const int rrows = tiled ? c.rk->rows_t[ti] : c.rk->rows;
     const int rnt = tiled ? c.rk->nt_t[ti] : c.rk->nt;
     const int rsm = tiled ? c.rk->smem_t[ti] : c.rk->smem;
-    const dim3 grow((c.H + rrows - 1) / rrows, nb), gcol(c.col_blocks(), nb);
+    const int cnt = tiled ? c.ck->nt_t : c.ck->nt;
+    const int csm = tiled ? c.ck->smem_gs_t : c.ck->smem_gs;
+    const dim3 grow((c.H + rrows - 1) / rrows, nb), gcol(strips, nb);
     // prologue (writes h_0 out when there is no iteration)
     hg::PassArgs a0 = a;
     if (n_iter == 0)
@@ -748,7 +762,7 @@ hg_status gs_class(hg_plan* p, const SizeClass& c, const GsCall& g, cudaStream_t
     }
     for (int it = 0; it < n_iter; ++it) {
       a.iter = it;
-      if ((s = launch(p, K_COL_GS, k_col[1], gcol, c.ck->nt, c.ck->smem_gs, a, st)) != HG_OK) return s;
+      if ((s = launch(p, K_COL_GS, k_col[1], gcol, cnt, csm, a, st)) != HG_OK) return s;
       const bool last = it == n_iter - 1;
       hg::PassArgs ar = last ? ao : a;
       ar.finalize = nmse_out != nullptr;  // the row pass first adds up this column pass's NMSE
@@ -757,7 +771,7 @@ hg_status gs_class(hg_plan* p, const SizeClass& c, const GsCall& g, cudaStream_t
     }
     a.iter = n_iter;
     a.fin_iter = n_iter;
-    if ((s = launch(p, K_COL_NMSE, k_col[0], gcol, c.ck->nt, c.ck->smem_gs, a, st)) != HG_OK) return s;
+    if ((s = launch(p, K_COL_NMSE, k_col[0], gcol, cnt, csm, a, st)) != HG_OK) return s;
     if (nmse_out && (s = launch(p, K_FINALIZE, (const void*)&hg::k_finalize<0>, dim3(1, nb), 32, 0, a, st)) != HG_OK)
       return s;
   }

@@ -59,14 +59,24 @@ struct RowCfg {
   static constexpr int SMEM = G::SM_ELEMS * 8;
 };
 
-// Column strip: C columns of length H, about 16 values per thread.  Widths measured on GB300 (GS,
-// 100 iterations): 2-column strips (256 / 512 threads, several CTAs per SM, so barriers span few
-// warps and the last wave is short) beat 8-column ones by 7-11 % at 2048 and 4096 rows and 12 % at
-// 512; at 1024 rows 8-column strips are 8 % faster; at 1080 rows (1080 x 1920) 4-column strips are
-// 14 % faster than 8 and 20 % faster than 2; 864 rows are indifferent.
-template <int H>
+// Column strip widths.  On a field tiled in column strips (GS), measured on GB300 (100
+// iterations): 2-column strips (256 / 512 threads, several CTAs per SM, so barriers span few warps
+// and the last wave is short) beat 8-column ones by 7-11 % at 2048 and 4096 rows and 12 % at 512;
+// at 1024 rows 8-column strips are 8 % faster; at 1080 rows (1080 x 1920) 4-column strips are 14 %
+// faster than 8 and 20 % faster than 2; 864 rows are indifferent.  On a row-major field a strip
+// reads C columns of every row, so it takes at least 4 (one 32-byte sector), 8 where shared memory
+// allows (4096 rows: 4).
+__host__ __device__ constexpr int tiled_cols(int h) {
+  return h >= 2048 ? 2 : (h == 1080 ? 4 : (h >= 640 ? 8 : (h >= 384 ? 2 : 16)));
+}
+__host__ __device__ constexpr int natural_cols(int h) {
+  return h >= 4096 ? 4 : (h == 1080 ? 4 : (h >= 640 ? 8 : 16));
+}
+
+// Column strip: C columns of length H, about 16 values per thread; TL: the tiled-field GS width.
+template <int H, bool TL = false>
 struct ColCfg {
-  static constexpr int C = H >= 2048 ? 2 : (H == 1080 ? 4 : (H >= 640 ? 8 : (H >= 384 ? 2 : 16)));
+  static constexpr int C = TL ? tiled_cols(H) : natural_cols(H);
   static constexpr int NT = pick_threads<typename PlanFor<H>::type>(H, C, value_budget(H), 1024);
   using G = Geo<H, C, NT, true>;
   using Fwd = typename PlanFor<H>::type;
@@ -542,8 +552,9 @@ __global__ void __launch_bounds__(RowCfg<W>::NT) k_row_fft(const __grid_constant
 // amplitude replacement R' = A R / |R| -> inverse column FFTs.  With REPLACE = false only the NMSE
 // is taken (last iteration) and the field is not written.
 template <int H, bool REPLACE, bool TILED>
-__global__ void __launch_bounds__(ColCfg<H>::NT, ColCfg<H>::MINB) k_col_gs(const __grid_constant__ PassArgs a) {
-  using K = ColCfg<H>;
+__global__ void __launch_bounds__(ColCfg<H, TILED>::NT, ColCfg<H, TILED>::MINB)
+    k_col_gs(const __grid_constant__ PassArgs a) {
+  using K = ColCfg<H, TILED>;
   using G = typename K::G;
   extern __shared__ __align__(16) float2 sm[];
   const int P = a.n_planes > 1 ? a.n_planes : 1;

@@ -35,12 +35,14 @@ struct RowKernels {
 };
 
 struct ColKernels {
-  int cols;
+  int cols;                 // strip width on a row-major field (all kernels but gs_t)
   int nt;
   int smem;
-  int smem_gs;              // dynamic shared memory of k_col_gs (exchange buffer + target strip)
+  int smem_gs;              // dynamic shared memory of k_col_gs / k_col_ospr (exchange + target strip)
   const void* gs[2];        // k_col_gs<REPLACE = false / true> (row-major field)
-  const void* gs_t[2];      // the same on a field tiled in this strip width
+  int tile;                 // strip width of the tiled GS field
+  int nt_t, smem_gs_t;      // threads and shared memory of gs_t
+  const void* gs_t[2];      // k_col_gs on the field tiled in strips of width tile
   const void* fft[2][2];    // k_col_fft<INV><POST>
   const void* ospr[3];      // k_col_ospr: [0] start only, [1] finish + start, [2] finish only
   const void* gd[2];        // k_col_gd<BWD = false / true>

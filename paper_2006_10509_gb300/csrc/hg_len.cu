@@ -92,6 +92,10 @@ ColKernels make_col() {
   c.smem_gs = K::SMEM_T;
   c.gs[0] = (const void*)&k_col_gs<N, false, false>;
   c.gs[1] = (const void*)&k_col_gs<N, true, false>;
+  using KT = ColCfg<N, true>;
+  c.tile = KT::C;
+  c.nt_t = KT::NT;
+  c.smem_gs_t = KT::SMEM_T;
   c.gs_t[0] = (const void*)&k_col_gs<N, false, true>;
   c.gs_t[1] = (const void*)&k_col_gs<N, true, true>;
   c.fft[0][0] = (const void*)&k_col_fft<N, false, false>;
@@ -131,8 +135,8 @@ void set_row_attrs(const RowKernels& r) {
 void set_col_attrs(const ColKernels& c) {
   allow_smem(&k_col_gs<HG_LEN, false, false>, c.smem_gs);
   allow_smem(&k_col_gs<HG_LEN, true, false>, c.smem_gs);
-  allow_smem(&k_col_gs<HG_LEN, false, true>, c.smem_gs);
-  allow_smem(&k_col_gs<HG_LEN, true, true>, c.smem_gs);
+  allow_smem(&k_col_gs<HG_LEN, false, true>, c.smem_gs_t);
+  allow_smem(&k_col_gs<HG_LEN, true, true>, c.smem_gs_t);
   allow_smem(&k_col_fft<HG_LEN, false, false>, c.smem);
   allow_smem(&k_col_fft<HG_LEN, false, true>, c.smem);
   allow_smem(&k_col_fft<HG_LEN, true, false>, c.smem);
