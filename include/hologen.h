@@ -220,8 +220,10 @@ HG_API int64_t hg_plan_launch_count(const hg_plan* plan);
  * interface).  hg_gs_run runs the size classes of a plan smallest first (each class one batched
  * launch per pass), so small holograms finish early.  With graph mode on, it captures the whole launch
  * sequence into a CUDA graph the first time it sees an argument set, and replays that graph with a
- * single launch while the arguments (pointers, n_iter, seed) stay the same.  Per-kernel timing is not
- * recorded inside graphs.
+ * single launch while the arguments (pointers, n_iter, seed) stay the same (hg_ospr_run likewise).
+ * A plan keeps one graph with timing off and one with timing on; the timed graph records the event
+ * pair of every kernel as graph nodes, and the timing totals take its latest replay only.  Outside
+ * graphs, GS passes of at most 2048 x 2048 pixels per launch use programmatic dependent launch.
  * hg_plan_item_latency synchronises and returns, for each item, the device time (ms, %globaltimer)
  * from the start of the last hg_gs_run to the end of its size class.
  */

@@ -16,6 +16,10 @@
 #include <string>
 #include <vector>
 
+#ifndef HG_PDL
+#define HG_PDL 1
+#endif
+
 #include "hologen.h"
 #include "hg_kernels.cuh"
 #include "hg_launch.h"
@@ -163,24 +167,32 @@ struct hg_plan {
   std::vector<size_t> class_order;  // size classes, smallest first
   unsigned long long* stamps = nullptr;  // [1 + classes]: run start, end of each class (%globaltimer)
   bool graph = false;
+  bool capturing = false;           // enqueueing into a graph capture
   cudaStream_t cap = nullptr;       // capture stream of graph mode
-  cudaGraphExec_t gexec = nullptr;
-  std::vector<uintptr_t> gkey;
-  int64_t graph_kernels = 0;
-  // timing facility
-  bool timing = false;
-  int64_t launches = 0;
+  // graph mode keeps one executable graph per timing state: [1] also records a pair of events
+  // around every kernel (graph nodes); the timing totals take its latest replay
   struct Pending {
     cudaEvent_t a, b;
     int kind;
   };
+  struct GraphSlot {
+    cudaGraphExec_t exec = nullptr;
+    std::vector<uintptr_t> key;
+    int64_t kernels = 0;
+    std::vector<Pending> events;
+    bool replayed = false;  // events hold a replay that has not been folded in yet
+  };
+  GraphSlot gslot[2];
+  // timing facility
+  bool timing = false;
+  int64_t launches = 0;
   std::vector<Pending> pending;
   std::vector<cudaEvent_t> event_pool;
   double kind_ms[K_NUM_KINDS] = {};
   int64_t kind_count[K_NUM_KINDS] = {};
 
   ~hg_plan() {
-    if (gexec) cudaGraphExecDestroy(gexec);
+    for (GraphSlot& g : gslot) drop_graph(g);
     if (cap) cudaStreamDestroy(cap);
     for (void* p : allocs) cudaFree(p);
     for (auto& q : pending) {
@@ -202,20 +214,40 @@ struct hg_plan {
     }
     return e;
   }
-  // folds completed timing events into the per-kind totals (device must be idle)
+  void add_time(const Pending& q) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, q.a, q.b) == cudaSuccess) {
+      kind_ms[q.kind] += ms;
+      kind_count[q.kind] += 1;
+    } else {
+      cudaGetLastError();
+    }
+  }
+  // folds completed timing events into the per-kind totals (device must be idle): stream launches,
+  // and the latest replay of the timed graph
   void fold() {
     for (auto& q : pending) {
-      float ms = 0.f;
-      if (cudaEventElapsedTime(&ms, q.a, q.b) == cudaSuccess) {
-        kind_ms[q.kind] += ms;
-        kind_count[q.kind] += 1;
-      } else {
-        cudaGetLastError();
-      }
+      add_time(q);
       event_pool.push_back(q.a);
       event_pool.push_back(q.b);
     }
     pending.clear();
+    for (GraphSlot& g : gslot)
+      if (g.replayed) {
+        for (auto& q : g.events) add_time(q);
+        g.replayed = false;
+      }
+  }
+  void drop_graph(GraphSlot& g) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    g.exec = nullptr;
+    g.key.clear();
+    for (auto& q : g.events) {
+      event_pool.push_back(q.a);
+      event_pool.push_back(q.b);
+    }
+    g.events.clear();
+    g.replayed = false;
   }
   template <class T>
   hg_status alloc(T** p, size_t count, const char* what) {
@@ -264,13 +296,36 @@ hg_status launch(hg_plan* p, int kind, const void* fn, dim3 grid, int nt, int sm
   if (p->timing) {
     ea = p->get_event();
     eb = p->get_event();
-    if (ea && eb) cudaEventRecord(ea, s);
+    // inside a graph capture the records must be external ones to become event-record nodes
+    if (ea && eb) cudaEventRecordWithFlags(ea, s, p->capturing ? cudaEventRecordExternal : cudaEventRecordDefault);
   }
-  const cudaError_t e = cudaLaunchKernel(fn, grid, dim3(nt), args, (size_t)smem, s);
+  cudaError_t e;
+  // GS passes (they wait for their predecessor in-kernel) of at most 2048^2 pixels per launch, on
+  // a stream: programmatic stream serialisation hides the launch gap between the passes (measured
+  // on GB300: 256^2 +39 %, 1024^2 +11 %, 2048^2 +2 %); larger launches ran slower with it (4096^2:
+  // -10 %), and so did replayed graphs (2048^2: 19.7k against 21.1k it/s without), which keep it off.
+  const bool pdl = HG_PDL && !p->timing && !p->capturing &&
+                   (kind == K_COL_GS || kind == K_ROW_GS || kind == K_COL_NMSE) &&
+                   (int64_t)a.H * a.W * a.n_items <= (int64_t)2048 * 2048;
+  if (pdl) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(nt);
+    cfg.dynamicSmemBytes = (size_t)smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr{};
+    attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr.val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelExC(&cfg, fn, args);
+  } else {
+    e = cudaLaunchKernel(fn, grid, dim3(nt), args, (size_t)smem, s);
+  }
   if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
   p->launches++;
   if (ea && eb) {
-    cudaEventRecord(eb, s);
+    cudaEventRecordWithFlags(eb, s, p->capturing ? cudaEventRecordExternal : cudaEventRecordDefault);
     p->pending.push_back({ea, eb, kind});
   } else {
     if (ea) p->event_pool.push_back(ea);
@@ -429,11 +484,11 @@ hg_status hg_plan_kernel_time(hg_plan* p, int32_t kind, double* total_ms, int64_
 hg_status hg_plan_set_graph(hg_plan* p, int32_t enabled) {
   if (!p) return fail(HG_ERR_INVALID_ARG, "plan is NULL");
   p->graph = enabled != 0;
-  if (!p->graph && p->gexec) {
+  if (!p->graph) {
     DeviceGuard g(p->device);
-    cudaGraphExecDestroy(p->gexec);
-    p->gexec = nullptr;
-    p->gkey.clear();
+    cudaDeviceSynchronize();
+    p->fold();
+    for (auto& slot : p->gslot) p->drop_graph(slot);
   }
   return HG_OK;
 }
@@ -798,37 +853,46 @@ hg_status gs_enqueue(hg_plan* p, const GsCall& g, cudaStream_t st) {
 hg_status run_maybe_graph(hg_plan* p, const std::vector<uintptr_t>& key,
                           const std::function<hg_status(cudaStream_t)>& enqueue, cudaStream_t st) {
   if (!p->graph) return enqueue(st);
-  if (!p->gexec || key != p->gkey) {
-    if (p->gexec) {
-      cudaGraphExecDestroy(p->gexec);
-      p->gexec = nullptr;
+  hg_plan::GraphSlot& g = p->gslot[p->timing ? 1 : 0];
+  if (!g.exec || key != g.key) {
+    if (g.exec) {
+      HG_CUDA(cudaDeviceSynchronize(), "device error");
+      p->fold();
+      p->drop_graph(g);
     }
-    const bool timing = p->timing;
     const int64_t launches0 = p->launches;
-    p->timing = false;  // no per-kernel events inside a captured graph
+    const size_t pending0 = p->pending.size();
     if (!p->cap) HG_CUDA(cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking), "capture stream");
     HG_CUDA(cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal), "graph capture");
+    p->capturing = true;
     const hg_status s = enqueue(p->cap);
+    p->capturing = false;
     cudaGraph_t graph = nullptr;
     const cudaError_t e = cudaStreamEndCapture(p->cap, &graph);
-    p->timing = timing;
-    p->graph_kernels = p->launches - launches0;
+    g.kernels = p->launches - launches0;
     p->launches = launches0;
+    // timing events recorded during the capture are nodes of this graph: they belong to the slot
+    g.events.assign(p->pending.begin() + pending0, p->pending.end());
+    p->pending.resize(pending0);
     if (s != HG_OK || e != cudaSuccess) {
       if (graph) cudaGraphDestroy(graph);
       cudaGetLastError();
+      p->drop_graph(g);
       return s != HG_OK ? s : cuda_fail(e, "graph capture");
     }
-    const cudaError_t ei = cudaGraphInstantiate(&p->gexec, graph, 0);
+    const cudaError_t ei = cudaGraphInstantiate(&g.exec, graph, 0);
     cudaGraphDestroy(graph);
     if (ei != cudaSuccess) {
-      p->gexec = nullptr;
+      g.exec = nullptr;
+      p->drop_graph(g);
       return cuda_fail(ei, "graph instantiate");
     }
-    p->gkey = key;
+    g.key = key;
   }
-  HG_CUDA(cudaGraphLaunch(p->gexec, st), "graph launch");
-  p->launches += p->graph_kernels;
+  // a timed graph's events are overwritten by every replay: the totals take the latest one
+  HG_CUDA(cudaGraphLaunch(g.exec, st), "graph launch");
+  p->launches += g.kernels;
+  g.replayed = !g.events.empty();
   return HG_OK;
 }
 

@@ -144,6 +144,18 @@ __device__ __forceinline__ void prefetch_contig(float* ts, const float* __restri
   cp_async_commit();
 }
 
+// ---------------------------------------------------------------- programmatic dependent launch
+
+// The GS passes are launched with programmatic stream serialisation: a pass may be scheduled
+// while its predecessor drains.  It waits here before reading anything an earlier kernel wrote,
+// then lets its own successor be scheduled (which happens once every CTA of this pass has got this
+// far, so a waiting successor never holds a slot that one of this pass's CTAs still needs).
+// Without that launch attribute the wait returns at once.
+__device__ __forceinline__ void pdl_wait_then_release() {
+  asm volatile("griddepcontrol.wait;\n" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+
 // ---------------------------------------------------------------- launch arguments
 
 // Per-launch argument block: up to kMaxBatch items of one size class.  Plan-owned buffers
@@ -483,6 +495,7 @@ __global__ void __launch_bounds__(RowCfg<W, TW>::NT, RowCfg<W, TW>::MINB) k_row_
   using G = typename K::G;
   extern __shared__ __align__(16) float2 sm[];
   const int t = threadIdx.x, k = blockIdx.y;
+  pdl_wait_then_release();
   if (a.finalize && blockIdx.x == 0 && t < 32) finalize_nmse(a, k);
   const int row0 = blockIdx.x * K::ROWS;
   const int H = a.H;
@@ -564,14 +577,15 @@ __global__ void __launch_bounds__(ColCfg<H, TILED>::NT, ColCfg<H, TILED>::MINB)
   const int slot = a.class_slot[k];
   float2* f = a.field + ((size_t)slot * P + p) * H * W;
   const float* A = a.target[k * P + p];
-  // with several planes each plane's amplitude is brought to the energy of a unit-modulus field
-  // (A_s = A sqrt(HW / sum A^2)); the common sqrt(HW) is dropped.  One plane needs no scale.
-  const float amp_scale = P > 1 ? (float)__ldcg(&a.stats[((size_t)slot * P + p) * 4 + 3]) : 1.f;
   float* ts = reinterpret_cast<float*>(sm + G::SM_ELEMS);  // the strip's target, [n][C]
   if (a.ttile)
     prefetch_contig<H * K::C, K::NT>(ts, a.ttile + (((size_t)slot * P + p) * gridDim.x + blockIdx.x) * H * K::C);
   else
     prefetch_strip<H, K::C, K::NT>(ts, A, col0, W);
+  pdl_wait_then_release();  // the targets were in place before the previous pass began
+  // with several planes each plane's amplitude is brought to the energy of a unit-modulus field
+  // (A_s = A sqrt(HW / sum A^2)); the common sqrt(HW) is dropped.  One plane needs no scale.
+  const float amp_scale = P > 1 ? (float)__ldcg(&a.stats[((size_t)slot * P + p) * 4 + 3]) : 1.f;
   // tiled: this strip is one contiguous [H][C] block
   float2* fs = TILED ? f + (size_t)blockIdx.x * H * K::C : f;
   float2 v[K::V];

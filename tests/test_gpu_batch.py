@@ -72,3 +72,30 @@ def test_batch_graph_replay_is_identical():
         assert all(np.array_equal(a, b) for a, b in zip(lv, outs_s[0]))
         assert np.array_equal(nm, outs_s[1])
     assert launches > 0
+
+
+@pytest.mark.gpu
+def test_timed_graph_replay_reports_one_replay_and_same_results():
+    """Graph mode with timing on: the timed graph (event nodes around every kernel) gives the same
+    results as the untimed one, and the timing totals hold exactly the latest replay's launches."""
+    import torch
+    import paper_2006_10509_gb300 as hg
+
+    dev = cuda_device()
+    a = torch.from_numpy(synth.blur_target(512, 512, 2.0, seed=11)).to(dev)
+    nm_plain = torch.zeros((1, 9), device=dev)
+    nm_timed = torch.zeros((1, 9), device=dev)
+    with hg.Plan([512], [512]) as plan:
+        plan.set_graph(True)
+        plan.gs([a], 8, seed=5, nmse_out=nm_plain)
+        plan.set_timing(True)
+        for _ in range(3):
+            plan.gs([a], 8, seed=5, nmse_out=nm_timed)
+        kt = plan.kernel_times()
+        plan.set_timing(False)
+        plan.gs([a], 8, seed=5, nmse_out=nm_plain)
+        plan.sync()
+    assert torch.equal(nm_plain, nm_timed)
+    # one replay: 8 column passes + 8 row passes (+ init, final NMSE pass, finalise, target re-layout)
+    assert kt["col_gs"][1] == 8 and kt["row_gs"][1] == 8
+    assert all(ms > 0 for ms, _ in kt.values())
