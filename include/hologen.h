@@ -73,8 +73,11 @@ typedef struct {
   int32_t n_planes;        /* replay planes P >= 1 (Fourier: must be 1) */
   const double* z_m;       /* Fresnel: P propagation distances (> 0); may be NULL for Fourier */
   int32_t quant_levels;    /* 0 continuous phase; 2 binary {0, pi}; N in 3..256 N-level */
-  uint32_t flags;          /* reserved, must be 0 */
+  uint32_t flags;          /* 0 or HG_PLAN_AUTOTUNE */
 } hg_plan_desc;
+
+/* hg_plan_create runs hg_plan_autotune before returning. */
+#define HG_PLAN_AUTOTUNE 1u
 
 /*
  * Fresnel model (single-FFT, reading of the paper's "Fresnel" keyword): SLM pixel (i, j) at
@@ -228,6 +231,25 @@ HG_API int64_t hg_plan_launch_count(const hg_plan* plan);
  * from the start of the last hg_gs_run to the end of its size class.
  */
 HG_API hg_status hg_plan_set_graph(hg_plan* plan, int32_t enabled);
+
+/*
+ * Autotuner (SURVEY's plan-owned "autotune choice"; no counterpart in the paper).  Single-plane GS
+ * keeps its field tiled in column strips so that a column pass reads its strip as one contiguous
+ * block; the strip width trades the column pass's CTA size against the row pass's access pattern.
+ * The plan starts from a measured default per column length.  hg_plan_autotune times, for every
+ * size class, a 6-iteration GS run (seeded start, zero target in its own scratch) with each width
+ * the class allows (2, 4, 8 or 16 columns, or a row-major field) and keeps the fastest; choices
+ * are cached per process by (device, H, W, items in the class, levels, propagation).  It
+ * synchronises `stream` before and after, allocates and frees one scratch target per class, does
+ * not count or time its own launches, and drops captured graphs.  Results of later runs do not
+ * depend on the width except for the order in which NMSE partial sums are added.
+ * hg_plan_strip_width returns the width in use for an item's size class (0: row-major field);
+ * hg_plan_set_strip_width sets it by hand (synchronises the device, drops captured graphs;
+ * HG_ERR_INVALID_ARG for a width the class does not allow).
+ */
+HG_API hg_status hg_plan_autotune(hg_plan* plan, void* stream);
+HG_API hg_status hg_plan_strip_width(const hg_plan* plan, int32_t item, int32_t* width_out);
+HG_API hg_status hg_plan_set_strip_width(hg_plan* plan, int32_t item, int32_t width);
 HG_API hg_status hg_plan_item_latency(hg_plan* plan, double* ms_out);
 
 /* Human-readable name of a status code (static string). */

@@ -23,12 +23,14 @@ __all__ = [
     "hg_propagate", "hg_gs_run", "hg_status_string", "hg_last_error", "hg_supported_length", "Plan",
     "hg_plan_set_timing", "hg_plan_reset_timing", "hg_plan_kernel_time", "hg_kernel_kind_name",
     "hg_plan_launch_count", "hg_gs_run_noalloc", "hg_ospr_run", "hg_gd_step", "hg_gd_forward",
-    "hg_gd_backward", "hologram_loss", "hg_plan_set_graph", "hg_plan_item_latency",
+    "hg_gd_backward", "hologram_loss", "hg_plan_set_graph", "hg_plan_item_latency", "hg_plan_autotune",
+    "hg_plan_strip_width", "hg_plan_set_strip_width", "HG_PLAN_AUTOTUNE",
 ]
 
 HG_OK, HG_ERR_INVALID_ARG, HG_ERR_UNSUPPORTED_SIZE, HG_ERR_OUT_OF_MEMORY = 0, 1, 2, 3
 HG_ERR_CUDA, HG_ERR_TIMEOUT, HG_ERR_INTERNAL = 4, 5, 6
 HG_FOURIER, HG_FRESNEL = 0, 1
+HG_PLAN_AUTOTUNE = 1  # plan flag: autotune the strip widths at creation
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB = None
@@ -83,6 +85,9 @@ _SIGNATURES = {
     "hg_plan_launch_count": (ctypes.c_int64, [_VP]),
     "hg_plan_set_graph": (ctypes.c_int, [_VP, ctypes.c_int32]),
     "hg_plan_item_latency": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double)]),
+    "hg_plan_autotune": (ctypes.c_int, [_VP, _VP]),
+    "hg_plan_strip_width": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
+    "hg_plan_set_strip_width": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32]),
     "hg_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "hg_last_error": (ctypes.c_char_p, []),
     "hg_supported_length": (ctypes.c_int32, [ctypes.c_int32]),
@@ -298,17 +303,31 @@ def hg_plan_item_latency(plan: int, n_items: int) -> list[float]:
     return list(out)
 
 
+def hg_plan_autotune(plan: int, stream=None):
+    _check(load().hg_plan_autotune(plan, _stream(stream)), "hg_plan_autotune")
+
+
+def hg_plan_strip_width(plan: int, item: int) -> int:
+    out = ctypes.c_int32()
+    _check(load().hg_plan_strip_width(plan, item, ctypes.byref(out)), "hg_plan_strip_width")
+    return out.value
+
+
+def hg_plan_set_strip_width(plan: int, item: int, width: int):
+    _check(load().hg_plan_set_strip_width(plan, item, width), "hg_plan_set_strip_width")
+
+
 class Plan:
     """Owning wrapper around a plan handle (destroyed on close / exit / garbage collection)."""
 
     def __init__(self, heights, widths, propagation=HG_FOURIER, wavelength_m=0.0, pitch_m=0.0, z_m=None,
-                 quant_levels=0):
+                 quant_levels=0, flags=0):
         self.heights = list(heights)
         self.widths = list(widths)
         self.n_planes = len(z_m) if z_m else 1
         self.quant_levels = quant_levels
         self.handle = hg_plan_create(self.heights, self.widths, propagation, wavelength_m, pitch_m, z_m,
-                                     quant_levels)
+                                     quant_levels, flags)
 
     def close(self):
         if self.handle is not None:
@@ -370,3 +389,12 @@ class Plan:
 
     def item_latency_ms(self) -> list[float]:
         return hg_plan_item_latency(self.handle, len(self.heights))
+
+    def autotune(self, stream=None):
+        hg_plan_autotune(self.handle, stream)
+
+    def strip_width(self, item: int) -> int:
+        return hg_plan_strip_width(self.handle, item)
+
+    def set_strip_width(self, item: int, width: int):
+        hg_plan_set_strip_width(self.handle, item, width)

@@ -13,6 +13,7 @@
 #include <cstring>
 #include <functional>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -119,16 +120,28 @@ struct SizeClass {
   std::vector<float2*> cx, cy;   // per plane (Fresnel)
   int row_blocks() const { return (H + rk->rows - 1) / rk->rows; }
   int col_blocks() const { return (W + ck->cols - 1) / ck->cols; }    // strips on a row-major field
-  int col_blocks_t() const { return (W + ck->tile - 1) / ck->tile; }  // strips of the tiled GS field
-  // sizes covering either strip width: partial sums per strip, strips x H x width target copies
-  size_t max_strips() const { return (size_t)std::max(col_blocks(), col_blocks_t()); }
+  // strip width of the tiled GS field (0: single-plane GS keeps the field row-major); the default
+  // rule at plan creation, or the autotuner's choice
+  int tile = 0;
+  int col_blocks_t() const { return (W + tile - 1) / tile; }  // strips of the tiled GS field
+  // sizes covering any strip width (the narrowest tiled one is 2): partial sums per strip, and the
+  // strips x H x width target copies
+  size_t max_strips() const { return (size_t)std::max(col_blocks(), (W + 1) / 2); }
   size_t max_strip_cols() const {
-    return std::max((size_t)col_blocks() * ck->cols, (size_t)col_blocks_t() * ck->tile);
+    return std::max((size_t)col_blocks() * ck->cols, (size_t)(W + 15) / 16 * 16);
   }
+  // whether the GS field can be tiled in strips of width w here (kernels exist, rows tile evenly)
+  bool tileable(int w, int planes) const;
 };
 
-// index of a column-strip tile width (2 / 4 / 8 / 16) in RowKernels' tiled tables
+// index of a column-strip tile width (2 / 4 / 8 / 16) in the kernels' tiled tables
 int tile_index(int cols) { return cols == 2 ? 0 : (cols == 4 ? 1 : (cols == 8 ? 2 : 3)); }
+
+bool SizeClass::tileable(int w, int planes) const {
+  if (planes != 1 || (w != 2 && w != 4 && w != 8 && w != 16) || W % w != 0) return false;
+  const int ti = tile_index(w);
+  return ck->tiled[ti].gs[0] != nullptr && rk->init_t[ti] != nullptr;
+}
 
 struct DeviceGuard {
   int prev = -1;
@@ -526,7 +539,7 @@ hg_status hg_plan_create(const hg_plan_desc* d, hg_plan** out) {
     return fail(HG_ERR_INVALID_ARG, "Fourier plans have exactly one plane");
   if (d->quant_levels < 0 || d->quant_levels == 1 || d->quant_levels > kMaxLevels)
     return fail(HG_ERR_INVALID_ARG, "quant_levels must be 0 or 2..%d", kMaxLevels);
-  if (d->flags != 0) return fail(HG_ERR_INVALID_ARG, "flags must be 0");
+  if (d->flags & ~HG_PLAN_AUTOTUNE) return fail(HG_ERR_INVALID_ARG, "unknown flags 0x%x", d->flags);
   if (d->propagation == HG_FRESNEL) {
     if (!(d->wavelength_m > 0) || !(d->pitch_m > 0) || !std::isfinite(d->wavelength_m) || !std::isfinite(d->pitch_m))
       return fail(HG_ERR_INVALID_ARG, "Fresnel plans need wavelength_m > 0 and pitch_m > 0");
@@ -588,6 +601,7 @@ hg_status hg_plan_create(const hg_plan_desc* d, hg_plan** out) {
     c.ck->set_attrs();
     const size_t n = c.items.size() * (size_t)p->P;
     if ((s = p->alloc(&c.field, n * c.H * c.W, "field workspace")) != HG_OK) return bail(s);
+    c.tile = c.tileable(c.ck->tile, p->P) ? c.ck->tile : 0;
     if ((s = p->alloc(&c.partials, n * 3 * c.max_strips(), "reduction scratch")) != HG_OK) return bail(s);
     if ((s = p->alloc(&c.stats, n * 4, "loss statistics")) != HG_OK) return bail(s);
     if ((s = p->alloc(&c.ttile, n * c.max_strip_cols() * c.H, "target tiles")) != HG_OK)
@@ -637,6 +651,7 @@ hg_status hg_plan_create(const hg_plan_desc* d, hg_plan** out) {
     return (size_t)p->classes[x].H * p->classes[x].W < (size_t)p->classes[y].H * p->classes[y].W;
   });
   if (cudaDeviceSynchronize() != cudaSuccess) return bail(cuda_fail(cudaGetLastError(), "plan set-up"));
+  if ((d->flags & HG_PLAN_AUTOTUNE) && (s = hg_plan_autotune(p, nullptr)) != HG_OK) return bail(s);
   *out = p;
   return HG_OK;
 }
@@ -748,9 +763,9 @@ hg_status gs_class(hg_plan* p, const SizeClass& c, const GsCall& g, cudaStream_t
     }
     // field layout: single-plane runs tile the field in column strips when the row length allows
     // (contiguous strips for the column pass), else row-major
-    const int ti = tile_index(c.ck->tile);
-    const bool tiled = P == 1 && c.rk->init_t[ti] != nullptr && c.W % c.ck->tile == 0;
-    const int strip = tiled ? c.ck->tile : c.ck->cols;
+    const bool tiled = P == 1 && c.tile > 0;
+    const int ti = tiled ? tile_index(c.tile) : 0;
+    const int strip = tiled ? c.tile : c.ck->cols;
     const int strips = tiled ? c.col_blocks_t() : c.col_blocks();
     a.col_blocks = strips;
     // targets re-laid out per column strip once per run (read by every column pass of the run)
@@ -793,12 +808,12 @@ hg_status gs_class(hg_plan* p, const SizeClass& c, const GsCall& g, cudaStream_t
     }
     const void* k_init = tiled ? c.rk->init_t[ti] : c.rk->init;
     const void* k_row[2] = {tiled ? c.rk->gs_t[ti][0] : c.rk->gs[0], tiled ? c.rk->gs_t[ti][1] : c.rk->gs[1]};
-    const void* k_col[2] = {tiled ? c.ck->gs_t[0] : c.ck->gs[0], tiled ? c.ck->gs_t[1] : c.ck->gs[1]};
+    const void* k_col[2] = {tiled ? c.ck->tiled[ti].gs[0] : c.ck->gs[0], tiled ? c.ck->tiled[ti].gs[1] : c.ck->gs[1]};
     const int rrows = tiled ? c.rk->rows_t[ti] : c.rk->rows;
     const int rnt = tiled ? c.rk->nt_t[ti] : c.rk->nt;
     const int rsm = tiled ? c.rk->smem_t[ti] : c.rk->smem;
-    const int cnt = tiled ? c.ck->nt_t : c.ck->nt;
-    const int csm = tiled ? c.ck->smem_gs_t : c.ck->smem_gs;
+    const int cnt = tiled ? c.ck->tiled[ti].nt : c.ck->nt;
+    const int csm = tiled ? c.ck->tiled[ti].smem_gs : c.ck->smem_gs;
     const dim3 grow((c.H + rrows - 1) / rrows, nb), gcol(strips, nb);
     // prologue (writes h_0 out when there is no iteration)
     hg::PassArgs a0 = a;
@@ -935,6 +950,123 @@ hg_status hg_gs_run(hg_plan* p, const float* const* target_amp, const float* con
       key.push_back((uintptr_t)(level_out ? level_out[i] : nullptr));
     }
   return run_maybe_graph(p, key, [&](cudaStream_t q) { return gs_enqueue(p, call, q); }, (cudaStream_t)stream);
+}
+
+// ---------------------------------------------------------------- autotuner
+//
+// For every size class of a single-plane plan, times a short GS run (6 iterations, seeded start, a
+// zero target in plan-owned scratch: the kernels' work does not depend on the values) with each
+// strip width the class allows -- 2 / 4 / 8 / 16 columns on the tiled field, or the row-major
+// field -- and keeps the fastest.  Choices are cached per process by (device, H, W, items in the
+// class, quantisation, propagation), so plans of the same shape reuse them.
+
+namespace {
+std::mutex g_tune_mu;
+std::map<std::vector<int64_t>, int> g_tune_cache;
+}  // namespace
+
+static hg_status autotune_class(hg_plan* p, SizeClass& c, cudaStream_t st) {
+  std::vector<int> cand;
+  for (int w : {2, 4, 8, 16})
+    if (c.tileable(w, p->P)) cand.push_back(w);
+  cand.push_back(0);  // row-major field
+  if (cand.size() == 1) {
+    c.tile = 0;
+    return HG_OK;
+  }
+  const std::vector<int64_t> key{p->device, c.H, c.W, (int64_t)c.items.size(), p->levels, p->propagation};
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      c.tile = it->second;
+      return HG_OK;
+    }
+  }
+  float* zero = nullptr;
+  HG_CUDA(cudaMalloc(&zero, (size_t)c.H * c.W * sizeof(float)), "autotune scratch");
+  struct Free {
+    float* q;
+    ~Free() { cudaFree(q); }
+  } guard{zero};
+  HG_CUDA(cudaMemsetAsync(zero, 0, (size_t)c.H * c.W * sizeof(float), st), "memset");
+  std::vector<const float*> targets(p->n_items * p->P, zero);
+  const GsCall call{targets.data(), nullptr, 1, 6, nullptr, nullptr, nullptr};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  HG_CUDA(cudaEventCreate(&e0), "event");
+  HG_CUDA(cudaEventCreate(&e1), "event");
+  float best_ms = 0.f;
+  int best = cand[0];
+  hg_status s = HG_OK;
+  for (int w : cand) {
+    c.tile = w;
+    if ((s = gs_class(p, c, call, st)) != HG_OK) break;  // warm-up
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < 3 && s == HG_OK; ++r) s = gs_class(p, c, call, st);
+    cudaEventRecord(e1, st);
+    if (s != HG_OK) break;
+    cudaError_t e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) {
+      s = cuda_fail(e, "autotune timing");
+      break;
+    }
+    if (w == cand[0] || ms < best_ms) {
+      best_ms = ms;
+      best = w;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c.tile = best;
+  if (s != HG_OK) return s;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune_cache[key] = best;
+  return HG_OK;
+}
+
+hg_status hg_plan_autotune(hg_plan* p, void* stream) {
+  if (!p) return fail(HG_ERR_INVALID_ARG, "plan is NULL");
+  DeviceGuard g(p->device);
+  if (!g.ok) return fail(HG_ERR_CUDA, "cannot select device %d", p->device);
+  const cudaStream_t st = (cudaStream_t)stream;
+  HG_CUDA(cudaStreamSynchronize(st), "device error");
+  // the tuning runs are neither timed nor counted, and captured graphs are rebuilt afterwards
+  const bool timing = p->timing;
+  const int64_t launches = p->launches;
+  p->timing = false;
+  hg_status s = HG_OK;
+  for (SizeClass& c : p->classes)
+    if ((s = autotune_class(p, c, st)) != HG_OK) break;
+  p->timing = timing;
+  p->launches = launches;
+  HG_CUDA(cudaStreamSynchronize(st), "device error");
+  for (auto& slot : p->gslot) p->drop_graph(slot);
+  return s;
+}
+
+hg_status hg_plan_set_strip_width(hg_plan* p, int32_t item, int32_t width) {
+  if (!p) return fail(HG_ERR_INVALID_ARG, "plan is NULL");
+  if (item < 0 || item >= p->n_items) return fail(HG_ERR_INVALID_ARG, "item %d out of range", item);
+  SizeClass& c = p->classes[p->item_class[item]];
+  if (width != 0 && !c.tileable(width, p->P))
+    return fail(HG_ERR_INVALID_ARG, "strip width %d is not available for %dx%d%s", width, c.H, c.W,
+                p->P != 1 ? " with several planes" : "");
+  DeviceGuard g(p->device);
+  if (!g.ok) return fail(HG_ERR_CUDA, "cannot select device %d", p->device);
+  HG_CUDA(cudaDeviceSynchronize(), "device error");
+  c.tile = width;
+  for (auto& slot : p->gslot) p->drop_graph(slot);
+  return HG_OK;
+}
+
+hg_status hg_plan_strip_width(const hg_plan* p, int32_t item, int32_t* width_out) {
+  if (!p) return fail(HG_ERR_INVALID_ARG, "plan is NULL");
+  if (item < 0 || item >= p->n_items) return fail(HG_ERR_INVALID_ARG, "item %d out of range", item);
+  if (!width_out) return fail(HG_ERR_INVALID_ARG, "width_out is NULL");
+  *width_out = p->classes[p->item_class[item]].tile;
+  return HG_OK;
 }
 
 hg_status hg_ospr_run(hg_plan* p, const float* const* target_amp, int32_t n_subframes, int32_t n_iter,

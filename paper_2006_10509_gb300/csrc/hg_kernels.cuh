@@ -73,10 +73,12 @@ __host__ __device__ constexpr int natural_cols(int h) {
   return h >= 4096 ? 4 : (h == 1080 ? 4 : (h >= 640 ? 8 : 16));
 }
 
-// Column strip: C columns of length H, about 16 values per thread; TL: the tiled-field GS width.
-template <int H, bool TL = false>
+// Column strip: C columns of length H, about 16 values per thread.  CW = 0: the row-major-field
+// width; CW > 0: a strip of the tiled GS field of that width (the plan's default is tiled_cols(H),
+// the autotuner may pick another).
+template <int H, int CW = 0>
 struct ColCfg {
-  static constexpr int C = TL ? tiled_cols(H) : natural_cols(H);
+  static constexpr int C = CW ? CW : natural_cols(H);
   static constexpr int NT = pick_threads<typename PlanFor<H>::type>(H, C, value_budget(H), 1024);
   using G = Geo<H, C, NT, true>;
   using Fwd = typename PlanFor<H>::type;
@@ -86,6 +88,9 @@ struct ColCfg {
   static constexpr int SMEM = G::SM_ELEMS * 8;
   static constexpr int SMEM_T = SMEM + H * C * 4;  // + the strip's target values (GS passes)
   static constexpr int MINB = hg_max(1, 1024 / NT);  // CTAs per SM the register budget is cut for
+  // the configuration exists: no thread past the value budget, the GS pass's shared memory fits
+  static constexpr bool FEASIBLE =
+      RValues<Fwd>::max_values(H, C, NT) <= value_budget(H) && SMEM_T <= 227 * 1024;
 };
 
 // Global index of field element (row, n) of an [H][W] item: row-major (TW = 0), or column-strip
@@ -563,11 +568,13 @@ __global__ void __launch_bounds__(RowCfg<W>::NT) k_row_fft(const __grid_constant
 
 // GS column pass: forward column FFTs -> NMSE partials of I = |R|^2 against T = A^2 and
 // amplitude replacement R' = A R / |R| -> inverse column FFTs.  With REPLACE = false only the NMSE
-// is taken (last iteration) and the field is not written.
-template <int H, bool REPLACE, bool TILED>
-__global__ void __launch_bounds__(ColCfg<H, TILED>::NT, ColCfg<H, TILED>::MINB)
+// is taken (last iteration) and the field is not written.  CT > 0: the field is tiled in column
+// strips of width CT, each CTA's strip one contiguous block; CT = 0: row-major.
+template <int H, bool REPLACE, int CT>
+__global__ void __launch_bounds__(ColCfg<H, CT>::NT, ColCfg<H, CT>::MINB)
     k_col_gs(const __grid_constant__ PassArgs a) {
-  using K = ColCfg<H, TILED>;
+  constexpr bool TILED = CT > 0;
+  using K = ColCfg<H, CT>;
   using G = typename K::G;
   extern __shared__ __align__(16) float2 sm[];
   const int P = a.n_planes > 1 ? a.n_planes : 1;

@@ -40,9 +40,13 @@ struct ColKernels {
   int smem;
   int smem_gs;              // dynamic shared memory of k_col_gs / k_col_ospr (exchange + target strip)
   const void* gs[2];        // k_col_gs<REPLACE = false / true> (row-major field)
-  int tile;                 // strip width of the tiled GS field
-  int nt_t, smem_gs_t;      // threads and shared memory of gs_t
-  const void* gs_t[2];      // k_col_gs on the field tiled in strips of width tile
+  // k_col_gs on the GS field tiled in strips of width 2 / 4 / 8 / 16 (gs nullptr where that
+  // configuration does not exist for this length); tile: the default width (tiled_cols)
+  struct Tiled {
+    int nt, smem_gs;
+    const void* gs[2];
+  } tiled[4];
+  int tile;
   const void* fft[2][2];    // k_col_fft<INV><POST>
   const void* ospr[3];      // k_col_ospr: [0] start only, [1] finish + start, [2] finish only
   const void* gd[2];        // k_col_gd<BWD = false / true>

@@ -82,6 +82,26 @@ RowKernels make_row() {
   return r;
 }
 
+template <int N, int C>
+void fill_col_tiled(ColKernels::Tiled& t) {
+  using K = ColCfg<N, C>;
+  if constexpr (K::FEASIBLE) {
+    t.nt = K::NT;
+    t.smem_gs = K::SMEM_T;
+    t.gs[0] = (const void*)&k_col_gs<N, false, C>;
+    t.gs[1] = (const void*)&k_col_gs<N, true, C>;
+  }
+}
+
+template <int N, int C>
+void set_col_tiled_attrs() {
+  using K = ColCfg<N, C>;
+  if constexpr (K::FEASIBLE) {
+    allow_smem(&k_col_gs<N, false, C>, K::SMEM_T);
+    allow_smem(&k_col_gs<N, true, C>, K::SMEM_T);
+  }
+}
+
 template <int N>
 ColKernels make_col() {
   using K = ColCfg<N>;
@@ -90,14 +110,13 @@ ColKernels make_col() {
   c.nt = K::NT;
   c.smem = K::SMEM;
   c.smem_gs = K::SMEM_T;
-  c.gs[0] = (const void*)&k_col_gs<N, false, false>;
-  c.gs[1] = (const void*)&k_col_gs<N, true, false>;
-  using KT = ColCfg<N, true>;
-  c.tile = KT::C;
-  c.nt_t = KT::NT;
-  c.smem_gs_t = KT::SMEM_T;
-  c.gs_t[0] = (const void*)&k_col_gs<N, false, true>;
-  c.gs_t[1] = (const void*)&k_col_gs<N, true, true>;
+  c.gs[0] = (const void*)&k_col_gs<N, false, 0>;
+  c.gs[1] = (const void*)&k_col_gs<N, true, 0>;
+  fill_col_tiled<N, 2>(c.tiled[0]);
+  fill_col_tiled<N, 4>(c.tiled[1]);
+  fill_col_tiled<N, 8>(c.tiled[2]);
+  fill_col_tiled<N, 16>(c.tiled[3]);
+  c.tile = tiled_cols(N);
   c.fft[0][0] = (const void*)&k_col_fft<N, false, false>;
   c.fft[0][1] = (const void*)&k_col_fft<N, false, true>;
   c.fft[1][0] = (const void*)&k_col_fft<N, true, false>;
@@ -133,10 +152,12 @@ void set_row_attrs(const RowKernels& r) {
 }
 
 void set_col_attrs(const ColKernels& c) {
-  allow_smem(&k_col_gs<HG_LEN, false, false>, c.smem_gs);
-  allow_smem(&k_col_gs<HG_LEN, true, false>, c.smem_gs);
-  allow_smem(&k_col_gs<HG_LEN, false, true>, c.smem_gs_t);
-  allow_smem(&k_col_gs<HG_LEN, true, true>, c.smem_gs_t);
+  allow_smem(&k_col_gs<HG_LEN, false, 0>, c.smem_gs);
+  allow_smem(&k_col_gs<HG_LEN, true, 0>, c.smem_gs);
+  set_col_tiled_attrs<HG_LEN, 2>();
+  set_col_tiled_attrs<HG_LEN, 4>();
+  set_col_tiled_attrs<HG_LEN, 8>();
+  set_col_tiled_attrs<HG_LEN, 16>();
   allow_smem(&k_col_fft<HG_LEN, false, false>, c.smem);
   allow_smem(&k_col_fft<HG_LEN, false, true>, c.smem);
   allow_smem(&k_col_fft<HG_LEN, true, false>, c.smem);

@@ -1,0 +1,107 @@
+"""Strip widths of the tiled GS field and the autotuner that picks them.
+
+Every width a size class allows (2, 4, 8 or 16 columns, or the row-major field) runs the same FFTs
+on the same values, so quantised levels and phases must be bitwise equal across widths; only the
+grouping of the NMSE partial sums changes, so NMSE agrees to float rounding.  The autotuner must
+pick one of the allowed widths and leave results unchanged.
+"""
+import numpy as np
+import pytest
+
+import synth
+from tests.helpers import cuda_device
+
+SIZES = [(512, 512), (2048, 1024), (1080, 1920), (256, 256)]
+
+
+def _inputs(h, w, seed):
+    return synth.blur_target(h, w, 2.0, seed=seed), synth.uniform_phase(h, w, seed=seed + 1)
+
+
+def _run(hg, dev, plan, a, p, n_iter, levels):
+    import torch
+
+    h, w = a.shape
+    ta, tp = torch.from_numpy(a).to(dev), torch.from_numpy(p).to(dev)
+    ph = torch.zeros((h, w), dtype=torch.float32, device=dev)
+    lv = torch.zeros((h, w), dtype=torch.uint8, device=dev) if levels else None
+    nm = torch.zeros((1, n_iter + 1), dtype=torch.float32, device=dev)
+    plan.gs([ta], n_iter, init_phase=[tp], phase_out=[ph], level_out=None if lv is None else [lv], nmse_out=nm)
+    plan.sync()
+    return ph.cpu().numpy(), None if lv is None else lv.cpu().numpy(), nm.cpu().numpy()[0]
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("h, w", SIZES)
+@pytest.mark.parametrize("levels", [0, 4])
+def test_every_strip_width_gives_the_same_hologram(h, w, levels):
+    import paper_2006_10509_gb300 as hg
+
+    dev = cuda_device()
+    a, p = _inputs(h, w, 300 + h + levels)
+    with hg.Plan([h], [w], quant_levels=levels) as plan:
+        ref = _run(hg, dev, plan, a, p, 5, levels)
+        tried = [plan.strip_width(0)]
+        for width in (0, 2, 4, 8, 16):
+            try:
+                plan.set_strip_width(0, width)
+            except hg.HologenError as e:
+                assert e.status == hg.HG_ERR_INVALID_ARG
+                continue
+            tried.append(width)
+            out = _run(hg, dev, plan, a, p, 5, levels)
+            assert np.array_equal(out[0], ref[0]), width
+            if levels:
+                assert np.array_equal(out[1], ref[1]), width
+            np.testing.assert_allclose(out[2], ref[2], rtol=1e-5, atol=1e-7)
+        assert 0 in tried and len(set(tried)) >= 2
+
+
+@pytest.mark.gpu
+def test_autotune_picks_an_allowed_width_and_keeps_results():
+    import paper_2006_10509_gb300 as hg
+
+    dev = cuda_device()
+    sizes = [(512, 512), (1024, 1024), (864, 1536)]
+    with hg.Plan([s[0] for s in sizes], [s[1] for s in sizes], quant_levels=4) as plan:
+        defaults = [plan.strip_width(i) for i in range(len(sizes))]
+        plan.autotune()
+        tuned = [plan.strip_width(i) for i in range(len(sizes))]
+    assert all(t in (0, 2, 4, 8, 16) for t in tuned)
+    # the flag runs the same tuning at creation (cached choices: identical)
+    with hg.Plan([s[0] for s in sizes], [s[1] for s in sizes], quant_levels=4, flags=hg.HG_PLAN_AUTOTUNE) as plan:
+        assert [plan.strip_width(i) for i in range(len(sizes))] == tuned
+        a, p = _inputs(512, 512, 77)
+        out = _run_item(hg, dev, plan, sizes, 0, a, p)
+    with hg.Plan([s[0] for s in sizes], [s[1] for s in sizes], quant_levels=4) as plan:
+        ref = _run_item(hg, dev, plan, sizes, 0, a, p)
+    assert np.array_equal(out[0], ref[0])
+    np.testing.assert_allclose(out[1], ref[1], rtol=1e-5, atol=1e-7)
+    assert len(defaults) == len(tuned)
+
+
+def _run_item(hg, dev, plan, sizes, item, a, p):
+    import torch
+
+    ta = [torch.from_numpy(synth.blur_target(h, w, 2.0, seed=900 + i)).to(dev) for i, (h, w) in enumerate(sizes)]
+    tp = [torch.from_numpy(synth.uniform_phase(h, w, seed=950 + i)).to(dev) for i, (h, w) in enumerate(sizes)]
+    ta[item] = torch.from_numpy(a).to(dev)
+    tp[item] = torch.from_numpy(p).to(dev)
+    lv = [torch.zeros(s, dtype=torch.uint8, device=dev) for s in sizes]
+    nm = torch.zeros((len(sizes), 5), dtype=torch.float32, device=dev)
+    plan.gs(ta, 4, init_phase=tp, level_out=lv, nmse_out=nm)
+    plan.sync()
+    return lv[item].cpu().numpy(), nm[item].cpu().numpy()
+
+
+@pytest.mark.gpu
+def test_strip_width_rejected_for_multiplane_plans():
+    import paper_2006_10509_gb300 as hg
+
+    with hg.Plan([256], [256], propagation=hg.HG_FRESNEL, wavelength_m=532e-9, pitch_m=8e-6,
+                 z_m=[0.05, 0.1]) as plan:
+        assert plan.strip_width(0) == 0
+        with pytest.raises(hg.HologenError):
+            plan.set_strip_width(0, 2)
+        plan.autotune()
+        assert plan.strip_width(0) == 0
