@@ -465,7 +465,8 @@ def run_batch(args):
 
 
 def run_config(args):
-    """The remaining single-GPU configurations, each timed over graph replays after warm-up:
+    """The remaining single-GPU configurations, each timed over graph replays after warm-up (GS
+    strip widths autotuned first):
     gs256:       Fourier GS 256^2, continuous, 20 iterations, smoothed-noise target (seed 1001), start
                  phase seed 1002 (latency-bound: the whole field is 512 KB).
     fresnel1024: Fresnel GS 1024^2 (532 nm, 8 um, z = 0.1 m), 8-level, 100 iterations, 50-spot target
@@ -510,6 +511,8 @@ def run_config(args):
         nm = torch.zeros((nt, ns), dtype=torch.float32, device=dev)
         run = lambda: plan.ospr(ts, ns, 0, 3000, bits_out=bits, nmse_out=nm)  # noqa: E731
         units, unit, bpu = nt * ns, "subframes/s", 44 * h * wd
+    plan.autotune()  # GS strip widths (OSPR keeps its row-major field)
+    width = plan.strip_width(0)
     plan.set_graph(True)
     for _ in range(args.warmup):
         run()
@@ -528,7 +531,7 @@ def run_config(args):
     line = {"workload": w, "value": units / (ms / 1e3), "unit": unit, "ms_per_run": ms,
             "alg_bytes_per_unit": bpu, "achieved_gb_s": gbs, "frac_of_hbm": gbs / peak, "peak_source": src,
             "final_nmse": nm.cpu().numpy()[:, -1].tolist()[:4], "steps": args.steps, "warmup": args.warmup,
-            "graph": True}
+            "graph": True, "autotuned_strip_width": width}
     plan.close()
     print(json.dumps(line))
 
