@@ -9,8 +9,8 @@ Fourier transform algorithms (HoloGenAlgGSCuda), One-Step Phase-Retrieval (HoloG
 Fourier and Fresnel holograms (keywords), an FFT handler (FFTHandlerCuda), a quantiser
 (QuantiserCuda), a normaliser and a randomiser -- but prints no equation for any of them.  Each
 module therefore writes out the published method the name refers to (Gerchberg & Saxton 1972;
-Fienup 1982; Cable, Buckley et al. 2004; Goodman's single-FFT Fresnel transform; Kingma & Ba 2015;
-Salmon et al. 2011) in plain numpy float64, and every reading taken where the paper is silent is
+Fienup 1982; Cable, Buckley et al. 2004; Pasienski & DeMarco 2008; Goodman's single-FFT Fresnel
+transform; Kingma & Ba 2015; Salmon et al. 2011) in plain numpy float64, and every reading taken where the paper is silent is
 stated in the docstring of the function that takes it.
 
 Pins (see tests/test_oracle_*.py): closed forms (delta, plane wave, Gaussian chirp transform),
@@ -25,6 +25,7 @@ Modules:
   project   SLM-plane projections (continuous / N-level / binary) and amplitude replacement
   metrics   optimal-scale intensity NMSE
   gs        Gerchberg-Saxton (single plane) and averaged-projection multi-plane GS
+  mraf      mixed-region amplitude freedom (signal window, mixing m) and region-of-interest NMSE
   philox    Philox4x32-10 counter-based generator
   ospr      One-Step Phase-Retrieval
   gd        gradient-descent (Wirtinger) loss, analytic gradient and Adam
