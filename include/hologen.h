@@ -130,6 +130,21 @@ HG_API hg_status hg_gs_run(hg_plan* plan, const float* const* target_amp, const 
                     float* nmse_out, void* stream);
 
 /*
+ * Mixed-region amplitude freedom (MRAF; Pasienski & DeMarco 2008): the reading taken here of the
+ * paper's "other iterative Fourier transform approaches" (section "Algorithm Libraries",
+ * HoloGenAlgGSCuda).  Same loop, arguments and outputs as hg_gs_run on a single-plane plan, except
+ * in the replay plane: with signal region S (signal_mask[i][px] != 0; a NULL array or entry means
+ * the whole plane) and mix m in (0, 1],
+ *   R' = m A_s R / |R| on S,   R' = (1 - m) R elsewhere,   A_s = A sqrt(HW / sum_S A^2),
+ * and nmse_out[i][k] is the NMSE of h_k over S only.  signal_mask: per item a device uint8 [H][W]
+ * (FFT order, like the target); read only.  Errors: HG_ERR_INVALID_ARG for a multi-plane plan or m
+ * outside (0, 1], plus those of hg_gs_run.
+ */
+HG_API hg_status hg_mraf_run(hg_plan* plan, const float* const* target_amp, const uint8_t* const* signal_mask,
+                             float mix, const float* const* init_phase, uint64_t seed, int32_t n_iter,
+                             float* const* phase_out, uint8_t* const* level_out, float* nmse_out, void* stream);
+
+/*
  * One-Step Phase-Retrieval (Cable, Buckley et al.; section "Algorithm Libraries",
  * HoloGenAlgOSPRCuda): for every item (target t) and subframe s = 0..n_subframes-1
  *   E = A exp(2 pi i u),  u = (x >> 8) 2^-24,  x = word 0 of Philox4x32-10 with counter

@@ -416,9 +416,11 @@ __global__ void k_tile_target(const __grid_constant__ hg::PassArgs a, int C, flo
   const float* A = a.target[k * P + p];
   const int H = a.H, W = a.W, col0 = blockIdx.x * C;
   float* dst = ttile + (((size_t)a.class_slot[k] * P + p) * gridDim.x + blockIdx.x) * (size_t)H * C;
+  const uint8_t* mask = a.mix > 0.f ? a.mask[k] : nullptr;  // MRAF: -1 marks the noise region
   for (int i = threadIdx.x; i < H * C; i += blockDim.x) {
     const int n = i / C, b = i % C;
-    dst[i] = col0 + b < W ? __ldg(&A[(size_t)n * W + col0 + b]) : 0.f;
+    const size_t px = (size_t)n * W + col0 + b;
+    dst[i] = col0 + b < W ? ((mask && !__ldg(&mask[px])) ? -1.f : __ldg(&A[px])) : 0.f;
   }
 }
 
@@ -430,10 +432,11 @@ __global__ void k_amp_energy(const __grid_constant__ hg::PassArgs a) {
   const int k = blockIdx.y / P, p = blockIdx.y % P;
   const int sp = a.class_slot[k] * P + p;
   const float* A = a.target[k * P + p];
+  const uint8_t* mask = a.mix > 0.f ? a.mask[k] : nullptr;  // MRAF: the signal region's energy
   const size_t n = (size_t)a.H * a.W;
   float e = 0.f;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    const float x = __ldg(&A[i]);
+    const float x = (mask && !__ldg(&mask[i])) ? 0.f : __ldg(&A[i]);
     e = fmaf(x, x, e);
   }
   hg::block_partials(e, 0.f, 0.f, a.partials + (size_t)sp * 3 * gridDim.x);
@@ -726,6 +729,8 @@ struct GsCall {
   float* const* phase_out;
   uint8_t* const* level_out;
   float* nmse_out;
+  const uint8_t* const* mask = nullptr;  // MRAF signal regions (per item, nullable)
+  float mix = 0.f;                       // MRAF mixing parameter (0: plain GS)
 };
 
 __global__ void k_stamp(unsigned long long* dst) {
@@ -760,7 +765,9 @@ hg_status gs_class(hg_plan* p, const SizeClass& c, const GsCall& g, cudaStream_t
       a.class_slot[k] = (int)(c0 + k);
       for (int q = 0; q < P; ++q) a.target[k * P + q] = target_amp[item * P + q];
       a.phase_in[k] = init_phase ? init_phase[item] : nullptr;
+      a.mask[k] = g.mask ? g.mask[item] : nullptr;
     }
+    a.mix = g.mix;
     // field layout: single-plane runs tile the field in column strips when the row length allows
     // (contiguous strips for the column pass), else row-major
     const bool tiled = P == 1 && c.tile > 0;
@@ -805,6 +812,12 @@ hg_status gs_class(hg_plan* p, const SizeClass& c, const GsCall& g, cudaStream_t
       if (nmse_out && (s = launch(p, K_FINALIZE, (const void*)&hg::k_finalize<0>, gfin, 32, 0, a, st)) != HG_OK)
         return s;
       continue;
+    }
+    if (g.mix > 0.f) {
+      // MRAF: the signal region's target energy, for the absolute scale of m A_s
+      const dim3 genergy(strips, nb), gfin(1, nb);
+      if ((s = launch(p, K_AMP_ENERGY, (const void*)&k_amp_energy, genergy, 256, 0, a, st)) != HG_OK) return s;
+      if ((s = launch(p, K_FINALIZE, (const void*)&hg::k_finalize<2>, gfin, 32, 0, a, st)) != HG_OK) return s;
     }
     const void* k_init = tiled ? c.rk->init_t[ti] : c.rk->init;
     const void* k_row[2] = {tiled ? c.rk->gs_t[ti][0] : c.rk->gs[0], tiled ? c.rk->gs_t[ti][1] : c.rk->gs[1]};
@@ -945,6 +958,50 @@ hg_status hg_gs_run(hg_plan* p, const float* const* target_amp, const float* con
   if (p->graph)
     for (int i = 0; i < p->n_items; ++i) {
       for (int q = 0; q < p->P; ++q) key.push_back((uintptr_t)target_amp[i * p->P + q]);
+      key.push_back((uintptr_t)(init_phase ? init_phase[i] : nullptr));
+      key.push_back((uintptr_t)(phase_out ? phase_out[i] : nullptr));
+      key.push_back((uintptr_t)(level_out ? level_out[i] : nullptr));
+    }
+  return run_maybe_graph(p, key, [&](cudaStream_t q) { return gs_enqueue(p, call, q); }, (cudaStream_t)stream);
+}
+
+hg_status hg_mraf_run(hg_plan* p, const float* const* target_amp, const uint8_t* const* signal_mask, float mix,
+                      const float* const* init_phase, uint64_t seed, int32_t n_iter, float* const* phase_out,
+                      uint8_t* const* level_out, float* nmse_out, void* stream) {
+  if (!p) return fail(HG_ERR_INVALID_ARG, "plan is NULL");
+  if (p->P != 1) return fail(HG_ERR_INVALID_ARG, "MRAF needs a single-plane plan");
+  if (!(mix > 0.f && mix <= 1.f)) return fail(HG_ERR_INVALID_ARG, "mix must be in (0, 1]");
+  if (n_iter < 0 || n_iter > 1000000) return fail(HG_ERR_INVALID_ARG, "n_iter must be 0..1000000");
+  if (!target_amp) return fail(HG_ERR_INVALID_ARG, "target_amp is NULL");
+  if (level_out && p->levels == 0) {
+    for (int i = 0; i < p->n_items; ++i)
+      if (level_out[i]) return fail(HG_ERR_INVALID_ARG, "level_out needs a quantised plan");
+  }
+  DeviceGuard g(p->device);
+  if (!g.ok) return fail(HG_ERR_CUDA, "cannot select device %d", p->device);
+  hg_status s;
+  for (int i = 0; i < p->n_items; ++i) {
+    const size_t px = (size_t)p->H[i] * p->W[i];
+    if ((s = check_ptr(p, target_amp[i], px * 4, 4, "target_amp", i)) != HG_OK) return s;
+    if (signal_mask && signal_mask[i] && (s = check_ptr(p, signal_mask[i], px, 1, "signal_mask", i)) != HG_OK)
+      return s;
+    if (init_phase && init_phase[i] && (s = check_ptr(p, init_phase[i], px * 4, 4, "init_phase", i)) != HG_OK)
+      return s;
+    if (phase_out && phase_out[i] && (s = check_ptr(p, phase_out[i], px * 4, 4, "phase_out", i)) != HG_OK) return s;
+    if (level_out && level_out[i] && (s = check_ptr(p, level_out[i], px, 1, "level_out", i)) != HG_OK) return s;
+  }
+  if (nmse_out && (s = check_ptr(p, nmse_out, (size_t)p->n_items * (n_iter + 1) * 4, 4, "nmse_out", 0)) != HG_OK)
+    return s;
+  GsCall call{target_amp, init_phase, seed, n_iter, phase_out, level_out, nmse_out};
+  call.mask = signal_mask;
+  call.mix = mix;
+  uint32_t mix_bits;
+  std::memcpy(&mix_bits, &mix, sizeof mix_bits);
+  std::vector<uintptr_t> key{3, (uintptr_t)n_iter, (uintptr_t)seed, (uintptr_t)nmse_out, (uintptr_t)mix_bits};
+  if (p->graph)
+    for (int i = 0; i < p->n_items; ++i) {
+      key.push_back((uintptr_t)target_amp[i]);
+      key.push_back((uintptr_t)(signal_mask ? signal_mask[i] : nullptr));
       key.push_back((uintptr_t)(init_phase ? init_phase[i] : nullptr));
       key.push_back((uintptr_t)(phase_out ? phase_out[i] : nullptr));
       key.push_back((uintptr_t)(level_out ? level_out[i] : nullptr));

@@ -181,6 +181,10 @@ struct PassArgs {
   const float2* lev;       // level field exp(2 pi i q / N), q < N
   const float* lev_phase;  // level phase 2 pi q / N
   float2* field;           // class field buffer: item k at field + k * H * W
+  // MRAF (mix > 0): per-item signal-region masks (nonzero = signal; nullptr = the whole plane) and
+  // the mixing parameter m; the target copy marks noise-region pixels with -1
+  const uint8_t* mask[kMaxBatch];
+  float mix;
   float2* partials;        // class partial sums (hi, lo): (slot, plane) at partials + (slot P + p) 3 col_blocks
   float* nmse;             // nmse_out of the run (device) or nullptr
   uint64_t seed;           // starting-phase seed when phase_in is null
@@ -591,8 +595,12 @@ __global__ void __launch_bounds__(ColCfg<H, CT>::NT, ColCfg<H, CT>::MINB)
     prefetch_strip<H, K::C, K::NT>(ts, A, col0, W);
   pdl_wait_then_release();  // the targets were in place before the previous pass began
   // with several planes each plane's amplitude is brought to the energy of a unit-modulus field
-  // (A_s = A sqrt(HW / sum A^2)); the common sqrt(HW) is dropped.  One plane needs no scale.
-  const float amp_scale = P > 1 ? (float)__ldcg(&a.stats[((size_t)slot * P + p) * 4 + 3]) : 1.f;
+  // (A_s = A sqrt(HW / sum A^2)); the common sqrt(HW) is dropped.  One plane needs no scale, except
+  // under MRAF, where the signal region m A_s meets the noise region's (1 - m) R: on this
+  // unnormalised forward transform (R_u = sqrt(HW) R) the signal amplitude is m A HW / sqrt(sum_S A^2).
+  const bool mraf = a.mix > 0.f;
+  const float esc = (P > 1 || mraf) ? (float)__ldcg(&a.stats[((size_t)slot * P + p) * 4 + 3]) : 1.f;
+  const float amp_scale = mraf ? a.mix * (float)H * (float)W * esc : esc;
   // tiled: this strip is one contiguous [H][C] block
   float2* fs = TILED ? f + (size_t)blockIdx.x * H * K::C : f;
   float2 v[K::V];
@@ -610,6 +618,10 @@ __global__ void __launch_bounds__(ColCfg<H, CT>::NT, ColCfg<H, CT>::MINB)
   for_each_slot<G, RLast<typename K::Fwd>::value>(t, [&](int s, int b, int n) {
     const float2 r = v[s];
     const float amp = ts[n * K::C + b];
+    if (mraf && amp < 0.f) {  // MRAF noise region: R' = (1 - m) R, outside the ROI NMSE
+      if (REPLACE) v[s] = c_scale(r, 1.f - a.mix);
+      return;
+    }
     const float i2 = fmaf(r.x, r.x, r.y * r.y);
     const float tt = amp * amp;
     s_it = fmaf(i2, tt, s_it);

@@ -2,10 +2,12 @@
 
 Comparison rules (GPU float32 vs oracle float64):
 * fields: relative L2 error <= 1e-4 per transform;
-* continuous phase: wrapped angle error <= 1e-4 rad on pixels whose oracle pre-projection field is
-  not tiny, |g| >= 1e-2 rms(g).  The phase of a small field is ill-conditioned: a float32 FFT
-  round trip leaves an absolute error of a few 1e-7 rms(g) on every pixel, i.e. ~3e-5 rad at
-  |g| = 1e-2 rms but ~3e-4 rad at 1e-3 rms.  At most 0.1 % of pixels may be exempt;
+* continuous phase: the SLM fields exp(i phi) agree to relative L2 <= 1e-4 (the field bound), and on
+  every pixel the phase error times |g| (g: the oracle's pre-projection field) stays within the
+  float32 rounding of the transforms, 8 u log2(HW) rms(g) with u = 2^-24.  The phase of a small field
+  is ill-conditioned: a float32 FFT round trip leaves an absolute error of order u log2(HW) rms(g)
+  on every pixel (measured on GB300: up to 3.4e-6 rms(g) at 2^22 pixels, u log2(HW) = 1.3e-6), i.e.
+  ~3e-4 rad at |g| = 1e-2 rms but ~3e-6 rad at a typical pixel;
 * quantised phase: level indices equal on >= 99.9 % of pixels, and every mismatch on a non-tiny
   pixel has an oracle pre-quantisation phase within 1e-4 rad of a level boundary;
 * NMSE: within 1 % relative.
@@ -48,13 +50,19 @@ def not_tiny(g) -> np.ndarray:
     return m >= TINY * np.sqrt(np.mean(m * m))
 
 
+ROUNDING_MULT = 8.0  # float32 transform rounding bound: ROUNDING_MULT * 2^-24 * log2(HW) * rms(g)
+
+
 def check_continuous_phase(phase_gpu, g_oracle, h_oracle):
-    ok = not_tiny(g_oracle)
-    assert np.mean(~ok) <= MAX_EXEMPT, f"{np.mean(~ok):.2e} of pixels exempt"
-    err = np.abs(wrap(np.asarray(phase_gpu, dtype=np.float64) - np.angle(h_oracle)))
-    worst = float(err[ok].max()) if np.any(ok) else 0.0
-    assert worst <= PHASE_TOL, f"max wrapped phase error {worst:.3e} rad"
-    return worst
+    phase_gpu = np.asarray(phase_gpu, dtype=np.float64)
+    assert rel_l2(np.exp(1j * phase_gpu), h_oracle) <= FIELD_TOL
+    m = np.abs(g_oracle)
+    rms = np.sqrt(np.mean(m * m))
+    err = np.abs(wrap(phase_gpu - np.angle(h_oracle)))
+    bound = ROUNDING_MULT * 2.0 ** -24 * np.log2(m.size) * rms
+    worst = float(np.max(err * m))
+    assert worst <= bound, f"phase error x |g| = {worst / rms:.3e} rms(g) > {bound / rms:.3e} rms(g)"
+    return float(np.max(err[not_tiny(g_oracle)])) if np.any(not_tiny(g_oracle)) else 0.0
 
 
 def check_levels(q_gpu, q_oracle, g_oracle, n_levels):
