@@ -472,7 +472,9 @@ def run_config(args):
     fresnel1024: Fresnel GS 1024^2 (532 nm, 8 um, z = 0.1 m), 8-level, 100 iterations, 50-spot target
                  (seed 2001), start phase seed 2002.
     ospr:        OSPR 1920x1080 (W x H), 16 point-symmetric smoothed-noise targets (seeds 3001..3016),
-                 24 binary subframes each, Philox seed 3000, the whole batch as one graph launch."""
+                 24 binary subframes each, Philox seed 3000, the whole batch as one graph launch.
+    mraf2048:    MRAF 2048^2, continuous, signal window rows and columns [1/8, 3/8) of the FFT-order
+                 plane, m = 0.5, 100 iterations, 50-spot target (seed 6001), start phase seed 6002."""
     import numpy as np
     import torch
 
@@ -501,6 +503,17 @@ def run_config(args):
                        quant_levels=8)
         nm = torch.zeros((1, n_iter + 1), dtype=torch.float32, device=dev)
         run = lambda: plan.gs([a], n_iter, init_phase=[p0], nmse_out=nm)  # noqa: E731
+        units, unit, bpu = n_iter, "it/s", 36 * h * wd
+    elif w == "mraf2048":
+        h = wd = 2048
+        n_iter = 100
+        a = torch.from_numpy(synth.spots_target(h, wd, 50, seed=6001)).to(dev)
+        p0 = torch.from_numpy(synth.uniform_phase(h, wd, seed=6002)).to(dev)
+        mask = torch.zeros((h, wd), dtype=torch.uint8, device=dev)
+        mask[h // 8: 3 * h // 8, wd // 8: 3 * wd // 8] = 1
+        plan = hg.Plan([h], [wd])
+        nm = torch.zeros((1, n_iter + 1), dtype=torch.float32, device=dev)
+        run = lambda: plan.mraf([a], 0.5, n_iter, signal_mask=[mask], init_phase=[p0], nmse_out=nm)  # noqa: E731
         units, unit, bpu = n_iter, "it/s", 36 * h * wd
     else:
         h, wd, nt, ns = 1080, 1920, 16, 24
@@ -627,10 +640,10 @@ def main():
     ap.add_argument("--cpu-iters", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="gs2048",
-                    choices=["gs2048", "batch", "gd", "gs256", "fresnel1024", "ospr"],
+                    choices=["gs2048", "batch", "gd", "gs256", "fresnel1024", "ospr", "mraf2048"],
                     help="gs2048: the headline line; batch: the mixed-size serving batch; "
                          "gd: gradient descent vs multi-plane GS, time to NMSE; gs256 / fresnel1024 / ospr: "
-                         "the other single-GPU configurations")
+                         "the other single-GPU configurations; mraf2048: the MRAF variant of GS")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -640,7 +653,7 @@ def main():
     if args.workload == "gd":
         run_gd(args)
         return
-    if args.workload in ("gs256", "fresnel1024", "ospr"):
+    if args.workload in ("gs256", "fresnel1024", "ospr", "mraf2048"):
         run_config(args)
         return
     if args.impl == "reference":
