@@ -13,6 +13,11 @@ RunIterations() (section "Algorithm Interface").  No formula is printed.  Readin
 with h_0 = P_SLM(exp(i phi_0)) (reading: the starting phase is projected so that every h_k is a
 realisable hologram).  ``nmse[k]`` for k = 0..n_iter is the NMSE of h_k; h_{n_iter} is the output.
 
+Illumination (AlgorithmCuda stores "target, illumination and starting images", section "Algorithm
+Libraries"): the SLM is lit with amplitude profile illum and only sets the phase, so the SLM-plane
+constraint set is {illum e^{i phi}} and its nearest-point projection is illum * P_SLM(g); A_s then
+carries the field energy sum illum^2 (reading: the target at the illuminated SLM's energy).
+
 Multi-plane GS (averaged projections; not in the paper -- the comparator of the gradient-descent
 optimiser): with P planes, chirps c_p and targets A_p,
 
@@ -30,18 +35,35 @@ from .metrics import nmse
 from .project import amplitude_replace, hologram_phase, slm_project
 
 
-def scaled_amplitude(a: np.ndarray) -> np.ndarray:
-    """A_s = A sqrt(HW / sum A^2): the replay amplitude with a unit-modulus field's energy."""
+def scaled_amplitude(a: np.ndarray, energy: float | None = None) -> np.ndarray:
+    """A_s = A sqrt(E / sum A^2): the replay amplitude carrying the SLM field's energy E (HW for a
+    unit-modulus field, sum illum^2 under an illumination profile)."""
     a = np.asarray(a, dtype=np.float64)
-    return a * np.sqrt(a.size / np.sum(a * a))
+    e = float(a.size) if energy is None else float(energy)
+    return a * np.sqrt(e / np.sum(a * a))
 
 
-def gs(target_amp, init_phase, n_iter: int, n_levels: int = 0, c=None):
-    """Single-plane GS.  Returns dict(h, phase, q, nmse[n_iter+1])."""
+def _illuminate(h: np.ndarray, illum) -> np.ndarray:
+    """The SLM field under an illumination amplitude profile (None: uniform, unit amplitude)."""
+    return h if illum is None else np.asarray(illum, dtype=np.float64) * h
+
+
+def _energy(h: np.ndarray, illum) -> float:
+    return float(h.size) if illum is None else float(np.sum(np.asarray(illum, dtype=np.float64) ** 2))
+
+
+def gs(target_amp, init_phase, n_iter: int, n_levels: int = 0, c=None, illum=None):
+    """Single-plane GS.  Returns dict(h, phase, q, nmse[n_iter+1]).
+
+    illum: the SLM illumination amplitude profile [H][W] (AlgorithmCuda keeps an illumination image,
+    section "Algorithm Libraries"); the SLM sets the phase only, so every SLM field is
+    h = illum * P_SLM(.) and A_s carries its energy sum illum^2.  None: uniform unit illumination.
+    """
     a = np.asarray(target_amp, dtype=np.float64)
     t = a * a
-    a_s = scaled_amplitude(a)
     h, q = slm_project(np.exp(1j * np.asarray(init_phase, dtype=np.float64)), n_levels)
+    h = _illuminate(h, illum)
+    a_s = scaled_amplitude(a, _energy(h, illum))
     curve = []
     for _ in range(n_iter):
         r = fft2(h if c is None else h * c)
@@ -50,31 +72,32 @@ def gs(target_amp, init_phase, n_iter: int, n_levels: int = 0, c=None):
         if c is not None:
             g = np.conj(c) * g
         h, q = slm_project(g, n_levels)
+        h = _illuminate(h, illum)
     r = fft2(h if c is None else h * c)
     curve.append(nmse(np.abs(r) ** 2, t))
     return {"h": h, "phase": hologram_phase(h), "q": q, "nmse": np.array(curve)}
 
 
-def gs_step(h, target_amp, n_levels: int = 0, c=None):
+def gs_step(h, target_amp, n_levels: int = 0, c=None, illum=None):
     """One GS iteration from a given SLM field h (teacher forcing).
 
     Returns dict(h, q, g) with g the pre-projection SLM-plane field conj(c) F^-1(R').
     """
     a = np.asarray(target_amp, dtype=np.float64)
-    a_s = scaled_amplitude(a)
     h = np.asarray(h, dtype=np.complex128)
+    a_s = scaled_amplitude(a, _energy(h, illum))
     r = fft2(h if c is None else h * c)
     g = fft2(amplitude_replace(r, a_s), inverse=True)
     if c is not None:
         g = np.conj(c) * g
     h1, q = slm_project(g, n_levels)
-    return {"h": h1, "q": q, "g": g}
+    return {"h": _illuminate(h1, illum), "q": q, "g": g}
 
 
-def replay_error(h, target_amp, c=None) -> float:
+def replay_error(h, target_amp, c=None, illum=None) -> float:
     """Fienup's error  sum (|F(h c)| - A_s)^2  (non-increasing along GS, any projection)."""
-    a_s = scaled_amplitude(target_amp)
     h = np.asarray(h, dtype=np.complex128)
+    a_s = scaled_amplitude(target_amp, _energy(h, illum))
     r = fft2(h if c is None else h * c)
     return float(np.sum((np.abs(r) - a_s) ** 2))
 

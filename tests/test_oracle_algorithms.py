@@ -240,3 +240,52 @@ def test_gd_decreases_loss():
     phi, ts, cs = _gd_problem(n=32, seed=99)
     out = gd.gd_run(phi, ts, cs, 30, 0.05)
     assert out["loss"][-1] < 0.5 * out["loss"][0]
+
+
+# ------------------------------------------------------------------ GS under an illumination profile
+
+
+def _gaussian_beam(h, w, waist):
+    y = np.arange(h) - (h - 1) / 2
+    x = np.arange(w) - (w - 1) / 2
+    return np.exp(-(y[:, None] ** 2 + x[None, :] ** 2) / (2 * waist ** 2))
+
+
+@pytest.mark.parametrize("n_levels", [0, 2, 4])
+def test_gs_unit_illumination_is_gs(n_levels):
+    a = synth.blur_target(20, 24, 2.0, seed=51).astype(np.float64)
+    phi0 = synth.uniform_phase(20, 24, seed=52).astype(np.float64)
+    ref = gs.gs(a, phi0, 5, n_levels)
+    out = gs.gs(a, phi0, 5, n_levels, illum=np.ones((20, 24)))
+    np.testing.assert_array_equal(out["h"], ref["h"])
+    np.testing.assert_array_equal(out["nmse"], ref["nmse"])
+
+
+@pytest.mark.parametrize("n_levels", [0, 4])
+def test_gs_constant_illumination_keeps_the_phases(n_levels):
+    a = synth.blur_target(20, 24, 2.0, seed=53).astype(np.float64)
+    phi0 = synth.uniform_phase(20, 24, seed=54).astype(np.float64)
+    ref = gs.gs(a, phi0, 5, n_levels)
+    out = gs.gs(a, phi0, 5, n_levels, illum=np.full((20, 24), 0.37))
+    assert np.allclose(out["h"], 0.37 * ref["h"], atol=1e-12)
+    assert np.allclose(out["nmse"], ref["nmse"], atol=1e-12)
+
+
+@pytest.mark.parametrize("n_levels", [0, 2, 8])
+@pytest.mark.parametrize("fresnel", [False, True])
+def test_gs_error_reduction_under_gaussian_illumination(n_levels, fresnel):
+    h_, w_ = 32, 40
+    a = synth.blur_target(h_, w_, 1.5, seed=55).astype(np.float64)
+    illum = _gaussian_beam(h_, w_, 9.0)
+    c = optics.chirp(h_, w_, LAM, PITCH, 0.02) if fresnel else None
+    h, _ = project.slm_project(np.exp(1j * synth.uniform_phase(h_, w_, seed=56).astype(np.float64)), n_levels)
+    h = illum * h
+    errs = [gs.replay_error(h, a, c, illum)]
+    for _ in range(25):
+        step = gs.gs_step(h, a, n_levels, c, illum)
+        h = step["h"]
+        assert np.allclose(np.abs(h), illum, atol=1e-12)
+        errs.append(gs.replay_error(h, a, c, illum))
+    e = np.array(errs)
+    assert np.all(e[1:] <= e[:-1] * (1 + 1e-12)), e
+    assert e[-1] < e[0]
