@@ -130,6 +130,17 @@ HG_API hg_status hg_gs_run(hg_plan* plan, const float* const* target_amp, const 
                     float* nmse_out, void* stream);
 
 /*
+ * SLM illumination (section "Algorithm Libraries": AlgorithmCuda stores "target, illumination and
+ * starting images").  illum_amp: host array of n_items device pointers to float32 [H][W]
+ * amplitude profiles (row-major, the SLM plane), or NULL entries for uniform unit illumination; a
+ * NULL array clears the setting.  The plan keeps the pointers (the caller keeps the buffers alive
+ * and unchanged while runs use them).  hg_gs_run then takes the SLM field as illum * P_SLM(g): the
+ * SLM sets the phase only.  Single-plane plans; hg_mraf_run, hg_ospr_run and the gradient-descent
+ * calls reject a plan that has a profile set (HG_ERR_INVALID_ARG).
+ */
+HG_API hg_status hg_plan_set_illumination(hg_plan* plan, const float* const* illum_amp);
+
+/*
  * Mixed-region amplitude freedom (MRAF; Pasienski & DeMarco 2008): the reading taken here of the
  * paper's "other iterative Fourier transform approaches" (section "Algorithm Libraries",
  * HoloGenAlgGSCuda).  Same loop, arguments and outputs as hg_gs_run on a single-plane plan, except

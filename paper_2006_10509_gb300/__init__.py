@@ -25,6 +25,7 @@ __all__ = [
     "hg_plan_launch_count", "hg_gs_run_noalloc", "hg_ospr_run", "hg_gd_step", "hg_gd_forward",
     "hg_gd_backward", "hologram_loss", "hg_plan_set_graph", "hg_plan_item_latency", "hg_plan_autotune",
     "hg_plan_strip_width", "hg_plan_set_strip_width", "HG_PLAN_AUTOTUNE", "hg_mraf_run",
+    "hg_plan_set_illumination",
 ]
 
 HG_OK, HG_ERR_INVALID_ARG, HG_ERR_UNSUPPORTED_SIZE, HG_ERR_OUT_OF_MEMORY = 0, 1, 2, 3
@@ -84,6 +85,7 @@ _SIGNATURES = {
     "hg_kernel_kind_name": (ctypes.c_char_p, [ctypes.c_int32]),
     "hg_plan_launch_count": (ctypes.c_int64, [_VP]),
     "hg_plan_set_graph": (ctypes.c_int, [_VP, ctypes.c_int32]),
+    "hg_plan_set_illumination": (ctypes.c_int, [_VP, _PP]),
     "hg_mraf_run": (ctypes.c_int, [_VP, _PP, _PP, ctypes.c_float, _PP, ctypes.c_uint64, ctypes.c_int32, _PP, _PP,
                                    _VP, _VP]),
     "hg_plan_item_latency": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double)]),
@@ -199,6 +201,11 @@ def hg_gs_run(plan: int, target_amp, init_phase=None, seed: int = 0, n_iter: int
     _check(load().hg_gs_run(plan, _ptr_array(target_amp), _ptr_array(init_phase), seed, n_iter,
                             _ptr_array(phase_out), _ptr_array(level_out),
                             None if nmse_out is None else _data_ptr(nmse_out), _stream(stream)), "hg_gs_run")
+
+
+def hg_plan_set_illumination(plan: int, illum_amp=None):
+    """Per-item SLM illumination amplitude tensors (None entries: uniform); None clears."""
+    _check(load().hg_plan_set_illumination(plan, _ptr_array(illum_amp)), "hg_plan_set_illumination")
 
 
 def hg_mraf_run(plan: int, target_amp, mix: float, signal_mask=None, init_phase=None, seed: int = 0,
@@ -404,6 +411,10 @@ class Plan:
 
     def item_latency_ms(self) -> list[float]:
         return hg_plan_item_latency(self.handle, len(self.heights))
+
+    def set_illumination(self, illum_amp=None):
+        self._illum = illum_amp  # the plan reads these buffers on every run: keep them alive
+        hg_plan_set_illumination(self.handle, illum_amp)
 
     def autotune(self, stream=None):
         hg_plan_autotune(self.handle, stream)

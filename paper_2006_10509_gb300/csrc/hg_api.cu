@@ -175,6 +175,7 @@ struct hg_plan {
   std::map<int, float2*> tw;
   float2* lev = nullptr;
   float* lev_phase = nullptr;
+  std::vector<const float*> illum;  // per item SLM illumination amplitude (nullptr: uniform)
   std::vector<void*> allocs;
   // run order, graphs and latency stamps
   std::vector<size_t> class_order;  // size classes, smallest first
@@ -766,6 +767,7 @@ hg_status gs_class(hg_plan* p, const SizeClass& c, const GsCall& g, cudaStream_t
       for (int q = 0; q < P; ++q) a.target[k * P + q] = target_amp[item * P + q];
       a.phase_in[k] = init_phase ? init_phase[item] : nullptr;
       a.mask[k] = g.mask ? g.mask[item] : nullptr;
+      a.illum[k] = p->illum.empty() ? nullptr : p->illum[item];
     }
     a.mix = g.mix;
     // field layout: single-plane runs tile the field in column strips when the row length allows
@@ -957,6 +959,7 @@ hg_status hg_gs_run(hg_plan* p, const float* const* target_amp, const float* con
   std::vector<uintptr_t> key{1, (uintptr_t)n_iter, (uintptr_t)seed, (uintptr_t)nmse_out};
   if (p->graph)
     for (int i = 0; i < p->n_items; ++i) {
+      key.push_back((uintptr_t)(p->illum.empty() ? nullptr : p->illum[i]));
       for (int q = 0; q < p->P; ++q) key.push_back((uintptr_t)target_amp[i * p->P + q]);
       key.push_back((uintptr_t)(init_phase ? init_phase[i] : nullptr));
       key.push_back((uintptr_t)(phase_out ? phase_out[i] : nullptr));
@@ -965,11 +968,30 @@ hg_status hg_gs_run(hg_plan* p, const float* const* target_amp, const float* con
   return run_maybe_graph(p, key, [&](cudaStream_t q) { return gs_enqueue(p, call, q); }, (cudaStream_t)stream);
 }
 
+hg_status hg_plan_set_illumination(hg_plan* p, const float* const* illum_amp) {
+  if (!p) return fail(HG_ERR_INVALID_ARG, "plan is NULL");
+  if (!illum_amp) {
+    p->illum.clear();
+    return HG_OK;
+  }
+  if (p->P != 1) return fail(HG_ERR_INVALID_ARG, "an illumination profile needs a single-plane plan");
+  DeviceGuard g(p->device);
+  if (!g.ok) return fail(HG_ERR_CUDA, "cannot select device %d", p->device);
+  hg_status s;
+  for (int i = 0; i < p->n_items; ++i)
+    if (illum_amp[i] &&
+        (s = check_ptr(p, illum_amp[i], (size_t)p->H[i] * p->W[i] * 4, 4, "illum_amp", i)) != HG_OK)
+      return s;
+  p->illum.assign(illum_amp, illum_amp + p->n_items);
+  return HG_OK;
+}
+
 hg_status hg_mraf_run(hg_plan* p, const float* const* target_amp, const uint8_t* const* signal_mask, float mix,
                       const float* const* init_phase, uint64_t seed, int32_t n_iter, float* const* phase_out,
                       uint8_t* const* level_out, float* nmse_out, void* stream) {
   if (!p) return fail(HG_ERR_INVALID_ARG, "plan is NULL");
   if (p->P != 1) return fail(HG_ERR_INVALID_ARG, "MRAF needs a single-plane plan");
+  if (!p->illum.empty()) return fail(HG_ERR_INVALID_ARG, "MRAF does not take an illumination profile");
   if (!(mix > 0.f && mix <= 1.f)) return fail(HG_ERR_INVALID_ARG, "mix must be in (0, 1]");
   if (n_iter < 0 || n_iter > 1000000) return fail(HG_ERR_INVALID_ARG, "n_iter must be 0..1000000");
   if (!target_amp) return fail(HG_ERR_INVALID_ARG, "target_amp is NULL");
@@ -1133,6 +1155,7 @@ hg_status hg_ospr_run(hg_plan* p, const float* const* target_amp, int32_t n_subf
   if (n_iter < 0 || n_iter > 10000) return fail(HG_ERR_INVALID_ARG, "n_iter must be 0..10000");
   if (!target_amp) return fail(HG_ERR_INVALID_ARG, "target_amp is NULL");
   if (p->P != 1) return fail(HG_ERR_INVALID_ARG, "OSPR needs a single-plane plan");
+  if (!p->illum.empty()) return fail(HG_ERR_INVALID_ARG, "OSPR does not take an illumination profile");
   DeviceGuard g(p->device);
   if (!g.ok) return fail(HG_ERR_CUDA, "cannot select device %d", p->device);
   hg_status s;
@@ -1224,6 +1247,7 @@ static hg_status gd_run(hg_plan* p, float* const* phase, const float* const* tar
   if (!p) return fail(HG_ERR_INVALID_ARG, "plan is NULL");
   if (!phase || !target_int) return fail(HG_ERR_INVALID_ARG, "phase / target_int is NULL");
   if (p->levels != 0) return fail(HG_ERR_INVALID_ARG, "gradient descent needs a continuous-phase plan");
+  if (!p->illum.empty()) return fail(HG_ERR_INVALID_ARG, "gradient descent does not take an illumination profile");
   if (adam) {
     if (!adam_m || !adam_v) return fail(HG_ERR_INVALID_ARG, "adam_m / adam_v is NULL");
     if (step < 1) return fail(HG_ERR_INVALID_ARG, "step must be >= 1");

@@ -185,6 +185,7 @@ struct PassArgs {
   // the mixing parameter m; the target copy marks noise-region pixels with -1
   const uint8_t* mask[kMaxBatch];
   float mix;
+  const float* illum[kMaxBatch];  // GS: SLM illumination amplitude [H][W] per item (nullptr: uniform)
   float2* partials;        // class partial sums (hi, lo): (slot, plane) at partials + (slot P + p) 3 col_blocks
   float* nmse;             // nmse_out of the run (device) or nullptr
   uint64_t seed;           // starting-phase seed when phase_in is null
@@ -488,6 +489,7 @@ __global__ void __launch_bounds__(RowCfg<W, TW>::NT, RowCfg<W, TW>::MINB) k_row_
       h = slm_project(e, a.n_levels, a.lev, q);
       if (po) po[p] = a.n_levels ? __ldg(&a.lev_phase[q]) : phase_0_2pi(h);
       if (lo) lo[p] = (uint8_t)q;
+      if (a.illum[k]) h = c_scale(h, __ldg(&a.illum[k][p]));  // the SLM only sets the phase
       if (a.cx) h = c_mul(h, c_mul(__ldg(&a.cx[n]), __ldg(&a.cy[row])));
     }
     v[s] = h;
@@ -529,6 +531,7 @@ __global__ void __launch_bounds__(RowCfg<W, TW>::NT, RowCfg<W, TW>::MINB) k_row_
       if (po) po[p] = a.n_levels ? __ldg(&a.lev_phase[q]) : phase_0_2pi(h);
       if (lo) lo[p] = (uint8_t)q;
     }
+    if (a.illum[k] && row < H) h = c_scale(h, __ldg(&a.illum[k][(size_t)row * W + n]));  // phase-only SLM
     if (a.cx) h = c_mul(h, c);
     v[s] = row < H ? h : make_float2(0.f, 0.f);
   });
