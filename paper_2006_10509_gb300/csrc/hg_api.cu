@@ -140,7 +140,7 @@ int tile_index(int cols) { return cols == 2 ? 0 : (cols == 4 ? 1 : (cols == 8 ? 
 bool SizeClass::tileable(int w, int planes) const {
   if (planes != 1 || (w != 2 && w != 4 && w != 8 && w != 16) || W % w != 0) return false;
   const int ti = tile_index(w);
-  return ck->tiled[ti].gs[0] != nullptr && rk->init_t[ti] != nullptr;
+  return ck->tiled[ti].gs[0][0] != nullptr && rk->init_t[ti][0] != nullptr;
 }
 
 struct DeviceGuard {
@@ -801,7 +801,7 @@ hg_status gs_class(hg_plan* p, const SizeClass& c, const GsCall& g, cudaStream_t
       if ((s = launch(p, K_ROW_MP_INIT, c.rk->mp_init[1], grow, c.rk->nt, c.rk->smem, a0, st)) != HG_OK) return s;
       for (int it = 0; it < n_iter; ++it) {
         a.iter = it;
-        if ((s = launch(p, K_COL_GS, c.ck->gs[1], gcol, c.ck->nt, c.ck->smem_gs, a, st)) != HG_OK) return s;
+        if ((s = launch(p, K_COL_GS, c.ck->gs[1][0], gcol, c.ck->nt, c.ck->smem_gs, a, st)) != HG_OK) return s;
         const bool last = it == n_iter - 1;
         hg::PassArgs ar = last ? ao : a;
         ar.finalize = nmse_out != nullptr;
@@ -810,7 +810,7 @@ hg_status gs_class(hg_plan* p, const SizeClass& c, const GsCall& g, cudaStream_t
       }
       a.iter = n_iter;
       a.fin_iter = n_iter;
-      if ((s = launch(p, K_COL_NMSE, c.ck->gs[0], gcol, c.ck->nt, c.ck->smem_gs, a, st)) != HG_OK) return s;
+      if ((s = launch(p, K_COL_NMSE, c.ck->gs[0][0], gcol, c.ck->nt, c.ck->smem_gs, a, st)) != HG_OK) return s;
       if (nmse_out && (s = launch(p, K_FINALIZE, (const void*)&hg::k_finalize<0>, gfin, 32, 0, a, st)) != HG_OK)
         return s;
       continue;
@@ -821,9 +821,15 @@ hg_status gs_class(hg_plan* p, const SizeClass& c, const GsCall& g, cudaStream_t
       if ((s = launch(p, K_AMP_ENERGY, (const void*)&k_amp_energy, genergy, 256, 0, a, st)) != HG_OK) return s;
       if ((s = launch(p, K_FINALIZE, (const void*)&hg::k_finalize<2>, gfin, 32, 0, a, st)) != HG_OK) return s;
     }
-    const void* k_init = tiled ? c.rk->init_t[ti] : c.rk->init;
-    const void* k_row[2] = {tiled ? c.rk->gs_t[ti][0] : c.rk->gs[0], tiled ? c.rk->gs_t[ti][1] : c.rk->gs[1]};
-    const void* k_col[2] = {tiled ? c.ck->tiled[ti].gs[0] : c.ck->gs[0], tiled ? c.ck->tiled[ti].gs[1] : c.ck->gs[1]};
+    // extended kernels only when the run uses MRAF or an illumination profile
+    bool lit = false;
+    for (int k = 0; k < nb; ++k) lit = lit || a.illum[k] != nullptr;
+    const int x = (g.mix > 0.f || lit) ? 1 : 0;
+    const void* k_init = tiled ? c.rk->init_t[ti][x] : c.rk->init[x];
+    const void* k_row[2] = {tiled ? c.rk->gs_t[ti][0][x] : c.rk->gs[0][x],
+                            tiled ? c.rk->gs_t[ti][1][x] : c.rk->gs[1][x]};
+    const void* k_col[2] = {tiled ? c.ck->tiled[ti].gs[0][x] : c.ck->gs[0][x],
+                            tiled ? c.ck->tiled[ti].gs[1][x] : c.ck->gs[1][x]};
     const int rrows = tiled ? c.rk->rows_t[ti] : c.rk->rows;
     const int rnt = tiled ? c.rk->nt_t[ti] : c.rk->nt;
     const int rsm = tiled ? c.rk->smem_t[ti] : c.rk->smem;
@@ -1217,7 +1223,7 @@ hg_status hg_ospr_run(hg_plan* p, const float* const* target_amp, int32_t n_subf
           ar.fin_iter = sf - 1;
           if ((s = launch(p, K_ROW_OSPR, c.rk->ospr[n_iter == 0], grow, c.rk->nt, rs, ar, st)) != HG_OK) return s;
           for (int it = 0; it < n_iter; ++it) {
-            if ((s = launch(p, K_COL_GS, c.ck->gs[1], gcol, c.ck->nt, c.ck->smem_gs, ag, st)) != HG_OK) return s;
+            if ((s = launch(p, K_COL_GS, c.ck->gs[1][0], gcol, c.ck->nt, c.ck->smem_gs, ag, st)) != HG_OK) return s;
             if ((s = launch(p, K_ROW_OSPR, c.rk->ospr[it == n_iter - 1], grow, c.rk->nt, rs, a, st)) != HG_OK)
               return s;
           }

@@ -459,7 +459,7 @@ __device__ __forceinline__ void store_row_slots(const float2 (&v)[K::V], float2*
 
 // GS prologue: h0 = P_SLM(exp(i phi0)) (phi0 given, or drawn from the seed), times the chirp,
 // forward row FFTs -> field.  h0 is written out when phase_out / level_out are set.
-template <int W, int TW>
+template <int W, int TW, bool EXT = false>
 __global__ void __launch_bounds__(RowCfg<W, TW>::NT, RowCfg<W, TW>::MINB) k_row_init(const __grid_constant__ PassArgs a) {
   using K = RowCfg<W, TW>;
   using G = typename K::G;
@@ -489,7 +489,7 @@ __global__ void __launch_bounds__(RowCfg<W, TW>::NT, RowCfg<W, TW>::MINB) k_row_
       h = slm_project(e, a.n_levels, a.lev, q);
       if (po) po[p] = a.n_levels ? __ldg(&a.lev_phase[q]) : phase_0_2pi(h);
       if (lo) lo[p] = (uint8_t)q;
-      if (a.illum[k]) h = c_scale(h, __ldg(&a.illum[k][p]));  // the SLM only sets the phase
+      if (EXT && a.illum[k]) h = c_scale(h, __ldg(&a.illum[k][p]));  // the SLM only sets the phase
       if (a.cx) h = c_mul(h, c_mul(__ldg(&a.cx[n]), __ldg(&a.cy[row])));
     }
     v[s] = h;
@@ -500,7 +500,7 @@ __global__ void __launch_bounds__(RowCfg<W, TW>::NT, RowCfg<W, TW>::MINB) k_row_
 
 // GS row pass: inverse row FFTs, conj chirp, SLM projection (optionally written out), chirp,
 // forward row FFTs.
-template <int W, bool OUT, int TW>
+template <int W, bool OUT, int TW, bool EXT = false>
 __global__ void __launch_bounds__(RowCfg<W, TW>::NT, RowCfg<W, TW>::MINB) k_row_gs(const __grid_constant__ PassArgs a) {
   using K = RowCfg<W, TW>;
   using G = typename K::G;
@@ -531,7 +531,7 @@ __global__ void __launch_bounds__(RowCfg<W, TW>::NT, RowCfg<W, TW>::MINB) k_row_
       if (po) po[p] = a.n_levels ? __ldg(&a.lev_phase[q]) : phase_0_2pi(h);
       if (lo) lo[p] = (uint8_t)q;
     }
-    if (a.illum[k] && row < H) h = c_scale(h, __ldg(&a.illum[k][(size_t)row * W + n]));  // phase-only SLM
+    if (EXT && a.illum[k] && row < H) h = c_scale(h, __ldg(&a.illum[k][(size_t)row * W + n]));  // phase-only SLM
     if (a.cx) h = c_mul(h, c);
     v[s] = row < H ? h : make_float2(0.f, 0.f);
   });
@@ -576,8 +576,9 @@ __global__ void __launch_bounds__(RowCfg<W>::NT) k_row_fft(const __grid_constant
 // GS column pass: forward column FFTs -> NMSE partials of I = |R|^2 against T = A^2 and
 // amplitude replacement R' = A R / |R| -> inverse column FFTs.  With REPLACE = false only the NMSE
 // is taken (last iteration) and the field is not written.  CT > 0: the field is tiled in column
-// strips of width CT, each CTA's strip one contiguous block; CT = 0: row-major.
-template <int H, bool REPLACE, int CT>
+// strips of width CT, each CTA's strip one contiguous block; CT = 0: row-major.  EXT instances
+// also take MRAF's mixed regions (the plain ones stay free of its per-pixel test).
+template <int H, bool REPLACE, int CT, bool EXT = false>
 __global__ void __launch_bounds__(ColCfg<H, CT>::NT, ColCfg<H, CT>::MINB)
     k_col_gs(const __grid_constant__ PassArgs a) {
   constexpr bool TILED = CT > 0;
@@ -601,7 +602,7 @@ __global__ void __launch_bounds__(ColCfg<H, CT>::NT, ColCfg<H, CT>::MINB)
   // (A_s = A sqrt(HW / sum A^2)); the common sqrt(HW) is dropped.  One plane needs no scale, except
   // under MRAF, where the signal region m A_s meets the noise region's (1 - m) R: on this
   // unnormalised forward transform (R_u = sqrt(HW) R) the signal amplitude is m A HW / sqrt(sum_S A^2).
-  const bool mraf = a.mix > 0.f;
+  const bool mraf = EXT && a.mix > 0.f;
   const float esc = (P > 1 || mraf) ? (float)__ldcg(&a.stats[((size_t)slot * P + p) * 4 + 3]) : 1.f;
   const float amp_scale = mraf ? a.mix * (float)H * (float)W * esc : esc;
   // tiled: this strip is one contiguous [H][C] block

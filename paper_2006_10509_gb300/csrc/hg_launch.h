@@ -17,12 +17,13 @@ struct RowKernels {
   int rows;      // rows per CTA
   int nt;        // threads per CTA
   int smem;      // dynamic shared memory bytes
-  const void* init;         // k_row_init (row-major field)
-  const void* gs[2];        // k_row_gs<OUT = false / true> (row-major field)
+  // [EXT]: the plain kernel, or the one that also applies an SLM illumination profile
+  const void* init[2];      // k_row_init (row-major field)
+  const void* gs[2][2];     // k_row_gs<OUT = false / true> (row-major field)
   // the same on a field tiled in column strips of width 2 / 4 / 8 / 16 (nullptr where the row
   // length does not allow it); rows / threads / shared memory of those tiles
-  const void* init_t[4];
-  const void* gs_t[4][2];
+  const void* init_t[4][2];
+  const void* gs_t[4][2][2];
   int rows_t[4], nt_t[4], smem_t[4];
   const void* fft[2][2];    // k_row_fft<INV><PRE>
   const void* ospr[2];      // k_row_ospr<BITS = false / true>
@@ -39,12 +40,13 @@ struct ColKernels {
   int nt;
   int smem;
   int smem_gs;              // dynamic shared memory of k_col_gs / k_col_ospr (exchange + target strip)
-  const void* gs[2];        // k_col_gs<REPLACE = false / true> (row-major field)
+  // [EXT]: the plain kernel, or the one that also takes MRAF's mixed regions
+  const void* gs[2][2];     // k_col_gs<REPLACE = false / true> (row-major field)
   // k_col_gs on the GS field tiled in strips of width 2 / 4 / 8 / 16 (gs nullptr where that
   // configuration does not exist for this length); tile: the default width (tiled_cols)
   struct Tiled {
     int nt, smem_gs;
-    const void* gs[2];
+    const void* gs[2][2];
   } tiled[4];
   int tile;
   const void* fft[2][2];    // k_col_fft<INV><POST>

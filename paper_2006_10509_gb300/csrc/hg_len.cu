@@ -34,9 +34,12 @@ template <int N, int TW>
 void fill_tiled(RowKernels& r, int i) {
   if constexpr (row_tileable<N, TW>()) {
     using K = RowCfg<N, TW>;
-    r.init_t[i] = (const void*)&k_row_init<N, TW>;
-    r.gs_t[i][0] = (const void*)&k_row_gs<N, false, TW>;
-    r.gs_t[i][1] = (const void*)&k_row_gs<N, true, TW>;
+    r.init_t[i][0] = (const void*)&k_row_init<N, TW, false>;
+    r.init_t[i][1] = (const void*)&k_row_init<N, TW, true>;
+    r.gs_t[i][0][0] = (const void*)&k_row_gs<N, false, TW, false>;
+    r.gs_t[i][0][1] = (const void*)&k_row_gs<N, false, TW, true>;
+    r.gs_t[i][1][0] = (const void*)&k_row_gs<N, true, TW, false>;
+    r.gs_t[i][1][1] = (const void*)&k_row_gs<N, true, TW, true>;
     r.rows_t[i] = K::ROWS;
     r.nt_t[i] = K::NT;
     r.smem_t[i] = K::SMEM;
@@ -46,9 +49,12 @@ void fill_tiled(RowKernels& r, int i) {
 template <int N, int TW>
 void set_tiled_attrs() {
   if constexpr (row_tileable<N, TW>()) {
-    allow_smem(&k_row_init<N, TW>, RowCfg<N, TW>::SMEM);
-    allow_smem(&k_row_gs<N, false, TW>, RowCfg<N, TW>::SMEM);
-    allow_smem(&k_row_gs<N, true, TW>, RowCfg<N, TW>::SMEM);
+    allow_smem(&k_row_init<N, TW, false>, RowCfg<N, TW>::SMEM);
+    allow_smem(&k_row_init<N, TW, true>, RowCfg<N, TW>::SMEM);
+    allow_smem(&k_row_gs<N, false, TW, false>, RowCfg<N, TW>::SMEM);
+    allow_smem(&k_row_gs<N, true, TW, false>, RowCfg<N, TW>::SMEM);
+    allow_smem(&k_row_gs<N, false, TW, true>, RowCfg<N, TW>::SMEM);
+    allow_smem(&k_row_gs<N, true, TW, true>, RowCfg<N, TW>::SMEM);
   }
 }
 
@@ -59,9 +65,12 @@ RowKernels make_row() {
   r.rows = K::ROWS;
   r.nt = K::NT;
   r.smem = K::SMEM;
-  r.init = (const void*)&k_row_init<N, 0>;
-  r.gs[0] = (const void*)&k_row_gs<N, false, 0>;
-  r.gs[1] = (const void*)&k_row_gs<N, true, 0>;
+  r.init[0] = (const void*)&k_row_init<N, 0, false>;
+  r.init[1] = (const void*)&k_row_init<N, 0, true>;
+  r.gs[0][0] = (const void*)&k_row_gs<N, false, 0, false>;
+  r.gs[0][1] = (const void*)&k_row_gs<N, false, 0, true>;
+  r.gs[1][0] = (const void*)&k_row_gs<N, true, 0, false>;
+  r.gs[1][1] = (const void*)&k_row_gs<N, true, 0, true>;
   fill_tiled<N, 2>(r, 0);
   fill_tiled<N, 4>(r, 1);
   fill_tiled<N, 8>(r, 2);
@@ -88,8 +97,10 @@ void fill_col_tiled(ColKernels::Tiled& t) {
   if constexpr (K::FEASIBLE) {
     t.nt = K::NT;
     t.smem_gs = K::SMEM_T;
-    t.gs[0] = (const void*)&k_col_gs<N, false, C>;
-    t.gs[1] = (const void*)&k_col_gs<N, true, C>;
+    t.gs[0][0] = (const void*)&k_col_gs<N, false, C, false>;
+    t.gs[0][1] = (const void*)&k_col_gs<N, false, C, true>;
+    t.gs[1][0] = (const void*)&k_col_gs<N, true, C, false>;
+    t.gs[1][1] = (const void*)&k_col_gs<N, true, C, true>;
   }
 }
 
@@ -97,8 +108,10 @@ template <int N, int C>
 void set_col_tiled_attrs() {
   using K = ColCfg<N, C>;
   if constexpr (K::FEASIBLE) {
-    allow_smem(&k_col_gs<N, false, C>, K::SMEM_T);
-    allow_smem(&k_col_gs<N, true, C>, K::SMEM_T);
+    allow_smem(&k_col_gs<N, false, C, false>, K::SMEM_T);
+    allow_smem(&k_col_gs<N, true, C, false>, K::SMEM_T);
+    allow_smem(&k_col_gs<N, false, C, true>, K::SMEM_T);
+    allow_smem(&k_col_gs<N, true, C, true>, K::SMEM_T);
   }
 }
 
@@ -110,8 +123,10 @@ ColKernels make_col() {
   c.nt = K::NT;
   c.smem = K::SMEM;
   c.smem_gs = K::SMEM_T;
-  c.gs[0] = (const void*)&k_col_gs<N, false, 0>;
-  c.gs[1] = (const void*)&k_col_gs<N, true, 0>;
+  c.gs[0][0] = (const void*)&k_col_gs<N, false, 0, false>;
+  c.gs[0][1] = (const void*)&k_col_gs<N, false, 0, true>;
+  c.gs[1][0] = (const void*)&k_col_gs<N, true, 0, false>;
+  c.gs[1][1] = (const void*)&k_col_gs<N, true, 0, true>;
   fill_col_tiled<N, 2>(c.tiled[0]);
   fill_col_tiled<N, 4>(c.tiled[1]);
   fill_col_tiled<N, 8>(c.tiled[2]);
@@ -131,9 +146,12 @@ ColKernels make_col() {
 }
 
 void set_row_attrs(const RowKernels& r) {
-  allow_smem(&k_row_init<HG_LEN, 0>, r.smem);
-  allow_smem(&k_row_gs<HG_LEN, false, 0>, r.smem);
-  allow_smem(&k_row_gs<HG_LEN, true, 0>, r.smem);
+  allow_smem(&k_row_init<HG_LEN, 0, false>, r.smem);
+  allow_smem(&k_row_init<HG_LEN, 0, true>, r.smem);
+  allow_smem(&k_row_gs<HG_LEN, false, 0, false>, r.smem);
+  allow_smem(&k_row_gs<HG_LEN, true, 0, false>, r.smem);
+  allow_smem(&k_row_gs<HG_LEN, false, 0, true>, r.smem);
+  allow_smem(&k_row_gs<HG_LEN, true, 0, true>, r.smem);
   set_tiled_attrs<HG_LEN, 2>();
   set_tiled_attrs<HG_LEN, 4>();
   set_tiled_attrs<HG_LEN, 8>();
@@ -152,8 +170,10 @@ void set_row_attrs(const RowKernels& r) {
 }
 
 void set_col_attrs(const ColKernels& c) {
-  allow_smem(&k_col_gs<HG_LEN, false, 0>, c.smem_gs);
-  allow_smem(&k_col_gs<HG_LEN, true, 0>, c.smem_gs);
+  allow_smem(&k_col_gs<HG_LEN, false, 0, false>, c.smem_gs);
+  allow_smem(&k_col_gs<HG_LEN, true, 0, false>, c.smem_gs);
+  allow_smem(&k_col_gs<HG_LEN, false, 0, true>, c.smem_gs);
+  allow_smem(&k_col_gs<HG_LEN, true, 0, true>, c.smem_gs);
   set_col_tiled_attrs<HG_LEN, 2>();
   set_col_tiled_attrs<HG_LEN, 4>();
   set_col_tiled_attrs<HG_LEN, 8>();

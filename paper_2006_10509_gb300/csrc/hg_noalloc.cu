@@ -213,21 +213,21 @@ extern "C" hg_status hg_gs_run_noalloc(int32_t height, int32_t width, int32_t qu
     a0.phase_out[0] = phase_out;
     a0.level_out[0] = level_out;
   }
-  if ((s = run_kernel(rk->init, grow, rk->nt, rk->smem, a0, st)) != HG_OK) return s;
+  if ((s = run_kernel(rk->init[0], grow, rk->nt, rk->smem, a0, st)) != HG_OK) return s;
   hg::PassArgs ao = a;
   ao.phase_out[0] = phase_out;
   ao.level_out[0] = level_out;
   for (int it = 0; it < n_iter; ++it) {
     a.iter = it;
-    if ((s = run_kernel(ck->gs[1], gcol, ck->nt, ck->smem_gs, a, st)) != HG_OK) return s;
+    if ((s = run_kernel(ck->gs[1][0], gcol, ck->nt, ck->smem_gs, a, st)) != HG_OK) return s;
     const bool last = it == n_iter - 1;
     hg::PassArgs ar = last ? ao : a;
     ar.finalize = nmse_out != nullptr;  // the row pass first adds up this column pass's NMSE
     ar.fin_iter = it;
-    if ((s = run_kernel(rk->gs[last], grow, rk->nt, rk->smem, ar, st)) != HG_OK) return s;
+    if ((s = run_kernel(rk->gs[last][0], grow, rk->nt, rk->smem, ar, st)) != HG_OK) return s;
   }
   a.iter = n_iter;
   a.fin_iter = n_iter;
-  if ((s = run_kernel(ck->gs[0], gcol, ck->nt, ck->smem_gs, a, st)) != HG_OK) return s;
+  if ((s = run_kernel(ck->gs[0][0], gcol, ck->nt, ck->smem_gs, a, st)) != HG_OK) return s;
   return nmse_out ? run_kernel((const void*)&hg::k_finalize<0>, dim3(1, 1), 32, 0, a, st) : HG_OK;
 }
