@@ -64,13 +64,14 @@ struct RowCfg {
 // and the last wave is short) beat 8-column ones by 7-11 % at 2048 and 4096 rows and 12 % at 512;
 // at 1024 rows 8-column strips are 8 % faster; at 1080 rows (1080 x 1920) 4-column strips are 14 %
 // faster than 8 and 20 % faster than 2; 864 rows are indifferent.  On a row-major field a strip
-// reads C columns of every row, so it takes at least 4 (one 32-byte sector), 8 where shared memory
-// allows (4096 rows: 4).
+// reads C columns of every row, so it takes at least 4 (one 32-byte sector): 4 at 1080 and from
+// 2048 rows (measured: the gradient-descent adjoint column pass at 2048^2, 3 planes, 131 us with 8
+// columns, 105 with 4), else 8, and 16 below 640 rows.
 __host__ __device__ constexpr int tiled_cols(int h) {
   return h >= 2048 ? 2 : (h == 1080 ? 4 : (h >= 640 ? 8 : (h >= 384 ? 2 : 16)));
 }
 __host__ __device__ constexpr int natural_cols(int h) {
-  return h >= 4096 ? 4 : (h == 1080 ? 4 : (h >= 640 ? 8 : 16));
+  return h >= 2048 ? 4 : (h == 1080 ? 4 : (h >= 640 ? 8 : 16));
 }
 
 // Column strip: C columns of length H, about 16 values per thread.  CW = 0: the row-major-field
@@ -848,8 +849,10 @@ __device__ __forceinline__ float2 chirp_at(const PassArgs& a, int p, int n, int 
 // Start of a multi-plane run: h = P_SLM(exp(i phi)) (PROJECT; else h = exp(i phi) exactly, for
 // gradient descent), then for every plane p: forward row FFTs of h c_p -> field p.
 // GD reads phi from a.phi[k]; GS from a.phase_in[k] or the seed.
+// (Capped at 64 registers: measured on GB300, 2048^2 with 3 planes, 98 -> 73 us despite a few
+// spills; k_row_mp keeps its 128 registers, which measured faster than any cap.)
 template <int W, bool PROJECT>
-__global__ void __launch_bounds__(RowCfg<W>::NT) k_row_mp_init(const __grid_constant__ PassArgs a) {
+__global__ void __launch_bounds__(RowCfg<W>::NT, RowCfg<W>::MINB) k_row_mp_init(const __grid_constant__ PassArgs a) {
   using K = RowCfg<W>;
   using G = typename K::G;
   constexpr int R0 = RFirst<typename K::Fwd>::value;
@@ -1024,8 +1027,9 @@ __global__ void __launch_bounds__(ColCfg<H>::NT, ColCfg<H>::MINB) k_col_gd(const
 // Gradient-descent backward row pass: g = sum_p conj(c_p) (inverse row FFTs of field p);
 // dL/dphi = 2 Im(g conj(e^{i phi})) (times *grad_scale); optional gradient out and Adam update of
 // phi, m, v in place.
+// (Capped at 64 registers: measured on GB300, 2048^2 with 3 planes, 145 -> 96 us despite spills.)
 template <int W>
-__global__ void __launch_bounds__(RowCfg<W>::NT) k_row_gd_bwd(const __grid_constant__ PassArgs a) {
+__global__ void __launch_bounds__(RowCfg<W>::NT, RowCfg<W>::MINB) k_row_gd_bwd(const __grid_constant__ PassArgs a) {
   using K = RowCfg<W>;
   using G = typename K::G;
   extern __shared__ __align__(16) float2 sm[];
