@@ -1,5 +1,5 @@
-"""Mixed-region amplitude freedom (MRAF), an iterative Fourier transform variant (FP64).  Test
-infrastructure only.
+"""Mixed-region amplitude freedom (MRAF) and hybrid input-output (HIO), iterative Fourier transform
+variants with a signal window (FP64).  Test infrastructure only.
 
 The paper's GS class covers "the Gerchberg-Saxton algorithm and other iterative Fourier transform
 approaches" (section "Algorithm Libraries", HoloGenAlgGSCuda) and keeps region-of-interest helpers
@@ -78,4 +78,40 @@ def mraf(target_amp, mask, mix: float, init_phase, n_iter: int, n_levels: int = 
         h, q = step["h"], step["q"]
     r = fft2(h if c is None else h * c)
     curve.append(roi_nmse(np.abs(r) ** 2, t, mask))
+    return {"h": h, "phase": hologram_phase(h), "q": q, "nmse": np.array(curve)}
+
+
+def hio(target_amp, mask, beta: float, init_phase, n_iter: int, n_levels: int = 0, c=None):
+    """Fienup's hybrid input-output with the replay plane as the constrained domain (FP64).
+
+    Reading of "other iterative Fourier transform approaches" (section "Algorithm Libraries"): HIO
+    (Fienup 1982) with the roles of the planes as in hologram design.  The input is a replay-plane
+    field X_k; the system maps it through the SLM constraint, h_k = P_SLM(conj(c) F^-1(X_k)), and
+    back, Y_k = F(h_k c).  Where the replay constraint applies -- the signal region S -- the new input
+    imposes the target, X_{k+1} = A_s Y_k / |Y_k|; elsewhere it feeds the output back negatively,
+    X_{k+1} = X_k - beta Y_k.  The loop starts from h_0 = P_SLM(exp(i phi_0)) with X_0 := Y_0 on N.
+    A_s as for MRAF (signal_amplitude); ``nmse[k]`` is the ROI NMSE of h_k.  With S the whole plane
+    it is plain GS.  Returns dict(h, phase, q, nmse[n_iter+1]).
+    """
+    a = np.asarray(target_amp, dtype=np.float64)
+    m = np.asarray(mask, dtype=bool)
+    t = a * a
+    a_s = signal_amplitude(a, m)
+    h, q = slm_project(np.exp(1j * np.asarray(init_phase, dtype=np.float64)), n_levels)
+    x = None
+    curve = []
+    for _ in range(n_iter):
+        y = fft2(h if c is None else h * c)
+        curve.append(roi_nmse(np.abs(y) ** 2, t, m))
+        if x is None:
+            x = y
+        mag = np.abs(y)
+        unit = np.where(mag > 0.0, y / np.where(mag > 0.0, mag, 1.0), 1.0 + 0.0j)
+        x = np.where(m, a_s * unit, x - beta * y)
+        g = fft2(x, inverse=True)
+        if c is not None:
+            g = np.conj(c) * g
+        h, q = slm_project(g, n_levels)
+    y = fft2(h if c is None else h * c)
+    curve.append(roi_nmse(np.abs(y) ** 2, t, m))
     return {"h": h, "phase": hologram_phase(h), "q": q, "nmse": np.array(curve)}

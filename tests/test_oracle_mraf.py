@@ -99,3 +99,63 @@ def test_roi_nmse_properties():
     assert mraf.roi_nmse(i, t, mask) == mraf.roi_nmse(i2, t2, mask)
     exact = np.where(mask, 2.5 * t, i)
     assert abs(mraf.roi_nmse(exact, t, mask)) < 1e-14
+
+
+# ------------------------------------------------------------------ hybrid input-output
+
+
+@pytest.mark.parametrize("n_levels", [0, 2, 4])
+@pytest.mark.parametrize("fresnel", [False, True])
+def test_hio_full_signal_region_is_gs(n_levels, fresnel):
+    h_, w_ = 24, 30
+    a = synth.blur_target(h_, w_, 2.0, seed=71).astype(np.float64)
+    phi = synth.uniform_phase(h_, w_, seed=72).astype(np.float64)
+    c = optics.chirp(h_, w_, LAM, PITCH, 0.05) if fresnel else None
+    ref = gs.gs(a, phi, 5, n_levels, c)
+    out = mraf.hio(a, np.ones((h_, w_), dtype=bool), 0.7, phi, 5, n_levels, c)
+    assert np.allclose(out["h"], ref["h"], atol=1e-10)
+    assert np.allclose(out["nmse"], ref["nmse"], atol=1e-12)
+
+
+def test_hio_two_steps_by_explicit_dft():
+    h_, w_ = 6, 8
+    rng = np.random.default_rng(73)
+    a = rng.random((h_, w_))
+    mask = _window(h_, w_, 1, 4, 2, 6)
+    phi0 = 2 * np.pi * rng.random((h_, w_))
+    beta = 0.8
+    out = mraf.hio(a, mask, beta, phi0, 2)
+    # the same two iterations with the DFT matrices and the update written element by element
+    e = sum(a[y, x] ** 2 for y in range(h_) for x in range(w_) if mask[y, x])
+    a_s = a * np.sqrt(h_ * w_ / e)
+    h = np.exp(1j * phi0)
+    x_in = None
+    for _ in range(2):
+        y_out = dft.dft2_bruteforce(h)
+        if x_in is None:
+            x_in = y_out.copy()
+        nxt = np.empty_like(y_out)
+        for yy in range(h_):
+            for xx in range(w_):
+                if mask[yy, xx]:
+                    nxt[yy, xx] = a_s[yy, xx] * y_out[yy, xx] / abs(y_out[yy, xx])
+                else:
+                    nxt[yy, xx] = x_in[yy, xx] - beta * y_out[yy, xx]
+        x_in = nxt
+        g = dft.dft2_bruteforce(x_in, inverse=True)
+        h = g / np.abs(g)
+    assert np.allclose(out["h"], h, atol=1e-12)
+
+
+def test_hio_keeps_the_signal_region_constraint_and_feeds_back():
+    """After one update the input equals A_s Y/|Y| on S and (1 - beta) Y_0 on N (X_0 = Y_0)."""
+    h_, w_ = 16, 16
+    a = synth.blur_target(h_, w_, 2.0, seed=74).astype(np.float64)
+    mask = _window(h_, w_, 2, 9, 3, 11)
+    phi0 = synth.uniform_phase(h_, w_, seed=75).astype(np.float64)
+    beta = 0.6
+    h1 = mraf.hio(a, mask, beta, phi0, 1)["h"]
+    y0 = fft2(np.exp(1j * phi0))
+    x1 = np.where(mask, mraf.signal_amplitude(a, mask) * y0 / np.abs(y0), (1 - beta) * y0)
+    g = fft2(x1, inverse=True)
+    assert np.allclose(h1, g / np.abs(g), atol=1e-12)
