@@ -515,6 +515,18 @@ def run_config(args):
         nm = torch.zeros((1, n_iter + 1), dtype=torch.float32, device=dev)
         run = lambda: plan.mraf([a], 0.5, n_iter, signal_mask=[mask], init_phase=[p0], nmse_out=nm)  # noqa: E731
         units, unit, bpu = n_iter, "it/s", 36 * h * wd
+    elif w == "hio2048":
+        h = wd = 2048
+        n_iter = 100
+        a = torch.from_numpy(synth.spots_target(h, wd, 50, seed=6001)).to(dev)
+        p0 = torch.from_numpy(synth.uniform_phase(h, wd, seed=6002)).to(dev)
+        mask = torch.zeros((h, wd), dtype=torch.uint8, device=dev)
+        mask[h // 8: 3 * h // 8, wd // 8: 3 * wd // 8] = 1
+        plan = hg.Plan([h], [wd])
+        nm = torch.zeros((1, n_iter + 1), dtype=torch.float32, device=dev)
+        run = lambda: plan.hio([a], 0.7, n_iter, signal_mask=[mask], init_phase=[p0], nmse_out=nm)  # noqa: E731
+        # GS's 36 B/px plus the stored input X read and written on the noise region
+        units, unit, bpu = n_iter, "it/s", 36 * h * wd + 16 * (h * wd - (h // 4) * (wd // 4))
     else:
         h, wd, nt, ns = 1080, 1920, 16, 24
         ts = [torch.from_numpy(synth.symmetrise(synth.blur_target(h, wd, SIGMA, seed=3001 + k))).to(dev)
@@ -640,10 +652,10 @@ def main():
     ap.add_argument("--cpu-iters", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="gs2048",
-                    choices=["gs2048", "batch", "gd", "gs256", "fresnel1024", "ospr", "mraf2048"],
+                    choices=["gs2048", "batch", "gd", "gs256", "fresnel1024", "ospr", "mraf2048", "hio2048"],
                     help="gs2048: the headline line; batch: the mixed-size serving batch; "
                          "gd: gradient descent vs multi-plane GS, time to NMSE; gs256 / fresnel1024 / ospr: "
-                         "the other single-GPU configurations; mraf2048: the MRAF variant of GS")
+                         "the other single-GPU configurations; mraf2048 / hio2048: the MRAF and HIO variants of GS")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -653,7 +665,7 @@ def main():
     if args.workload == "gd":
         run_gd(args)
         return
-    if args.workload in ("gs256", "fresnel1024", "ospr", "mraf2048"):
+    if args.workload in ("gs256", "fresnel1024", "ospr", "mraf2048", "hio2048"):
         run_config(args)
         return
     if args.impl == "reference":

@@ -135,8 +135,8 @@ HG_API hg_status hg_gs_run(hg_plan* plan, const float* const* target_amp, const 
  * amplitude profiles (row-major, the SLM plane), or NULL entries for uniform unit illumination; a
  * NULL array clears the setting.  The plan keeps the pointers (the caller keeps the buffers alive
  * and unchanged while runs use them).  hg_gs_run then takes the SLM field as illum * P_SLM(g): the
- * SLM sets the phase only.  Single-plane plans; hg_mraf_run, hg_ospr_run and the gradient-descent
- * calls reject a plan that has a profile set (HG_ERR_INVALID_ARG).
+ * SLM sets the phase only.  Single-plane plans; hg_mraf_run, hg_hio_run, hg_ospr_run and the
+ * gradient-descent calls reject a plan that has a profile set (HG_ERR_INVALID_ARG).
  */
 HG_API hg_status hg_plan_set_illumination(hg_plan* plan, const float* const* illum_amp);
 
@@ -154,6 +154,21 @@ HG_API hg_status hg_plan_set_illumination(hg_plan* plan, const float* const* ill
 HG_API hg_status hg_mraf_run(hg_plan* plan, const float* const* target_amp, const uint8_t* const* signal_mask,
                              float mix, const float* const* init_phase, uint64_t seed, int32_t n_iter,
                              float* const* phase_out, uint8_t* const* level_out, float* nmse_out, void* stream);
+
+/*
+ * Hybrid input-output (HIO; Fienup 1982) with the replay plane as the constrained domain: a second
+ * reading of the paper's "other iterative Fourier transform approaches" (section "Algorithm
+ * Libraries").  Arguments and outputs as hg_mraf_run, with feedback beta in (0, 2] in place of mix.
+ * The input X is a replay-plane field; h_k = P_SLM(conj(c) F^-1(X_k)), Y_k = F(h_k c) and
+ *   X_{k+1} = A_s Y_k / |Y_k| on S,   X_{k+1} = X_k - beta Y_k elsewhere,   X_0 = Y_0,
+ * A_s as for MRAF; nmse_out[i][k] is the NMSE of h_k over S.  With S the whole plane it is GS.  The
+ * plan allocates an input buffer (8 bytes per pixel) on the first call.  Errors: HG_ERR_INVALID_ARG
+ * for a multi-plane plan, a plan with an illumination profile or beta outside (0, 2], plus those
+ * of hg_gs_run.
+ */
+HG_API hg_status hg_hio_run(hg_plan* plan, const float* const* target_amp, const uint8_t* const* signal_mask,
+                            float beta, const float* const* init_phase, uint64_t seed, int32_t n_iter,
+                            float* const* phase_out, uint8_t* const* level_out, float* nmse_out, void* stream);
 
 /*
  * One-Step Phase-Retrieval (Cable, Buckley et al.; section "Algorithm Libraries",

@@ -81,6 +81,25 @@ def mraf(target_amp, mask, mix: float, init_phase, n_iter: int, n_levels: int = 
     return {"h": h, "phase": hologram_phase(h), "q": q, "nmse": np.array(curve)}
 
 
+def hio_step(h, x, target_amp, mask, beta: float, n_levels: int = 0, c=None):
+    """One HIO iteration from SLM field h_k and replay-plane input X_k (None for k = 0: X_0 = Y_0).
+    Returns dict(h, q, g, x) with g the pre-projection SLM-plane field and x = X_{k+1}."""
+    m = np.asarray(mask, dtype=bool)
+    a_s = signal_amplitude(target_amp, m)
+    h = np.asarray(h, dtype=np.complex128)
+    y = fft2(h if c is None else h * c)
+    if x is None:
+        x = y
+    mag = np.abs(y)
+    unit = np.where(mag > 0.0, y / np.where(mag > 0.0, mag, 1.0), 1.0 + 0.0j)
+    x_new = np.where(m, a_s * unit, x - beta * y)
+    g = fft2(x_new, inverse=True)
+    if c is not None:
+        g = np.conj(c) * g
+    h1, q = slm_project(g, n_levels)
+    return {"h": h1, "q": q, "g": g, "x": x_new}
+
+
 def hio(target_amp, mask, beta: float, init_phase, n_iter: int, n_levels: int = 0, c=None):
     """Fienup's hybrid input-output with the replay plane as the constrained domain (FP64).
 
@@ -96,22 +115,14 @@ def hio(target_amp, mask, beta: float, init_phase, n_iter: int, n_levels: int = 
     a = np.asarray(target_amp, dtype=np.float64)
     m = np.asarray(mask, dtype=bool)
     t = a * a
-    a_s = signal_amplitude(a, m)
     h, q = slm_project(np.exp(1j * np.asarray(init_phase, dtype=np.float64)), n_levels)
     x = None
     curve = []
     for _ in range(n_iter):
         y = fft2(h if c is None else h * c)
         curve.append(roi_nmse(np.abs(y) ** 2, t, m))
-        if x is None:
-            x = y
-        mag = np.abs(y)
-        unit = np.where(mag > 0.0, y / np.where(mag > 0.0, mag, 1.0), 1.0 + 0.0j)
-        x = np.where(m, a_s * unit, x - beta * y)
-        g = fft2(x, inverse=True)
-        if c is not None:
-            g = np.conj(c) * g
-        h, q = slm_project(g, n_levels)
+        step = hio_step(h, x, a, m, beta, n_levels, c)
+        h, q, x = step["h"], step["q"], step["x"]
     y = fft2(h if c is None else h * c)
     curve.append(roi_nmse(np.abs(y) ** 2, t, m))
     return {"h": h, "phase": hologram_phase(h), "q": q, "nmse": np.array(curve)}

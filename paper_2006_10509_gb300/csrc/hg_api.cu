@@ -116,6 +116,7 @@ struct SizeClass {
   float2* partials = nullptr;    // [slot][plane][3 * col_blocks] (hi, lo) pairs
   float* acc = nullptr;          // [slot][H][W] OSPR accumulated intensity (allocated on first use)
   float* ttile = nullptr;        // [slot][plane][strip][H][C] targets re-laid out for the GS column passes
+  float2* hio = nullptr;         // [slot][strip][H][C] HIO replay-plane input (allocated on first use)
   double* stats = nullptr;       // [slot][plane][4] gradient-descent loss statistics
   std::vector<float2*> cx, cy;   // per plane (Fresnel)
   int row_blocks() const { return (H + rk->rows - 1) / rk->rows; }
@@ -731,7 +732,9 @@ struct GsCall {
   uint8_t* const* level_out;
   float* nmse_out;
   const uint8_t* const* mask = nullptr;  // MRAF signal regions (per item, nullable)
-  float mix = 0.f;                       // MRAF mixing parameter (0: plain GS)
+  float mix = 0.f;                       // MRAF mixing parameter (0: plain GS; 1 under HIO)
+  bool hio = false;                      // HIO: noise-region feedback X' = X - beta Y
+  float beta = 0.f;
 };
 
 __global__ void k_stamp(unsigned long long* dst) {
@@ -770,6 +773,8 @@ hg_status gs_class(hg_plan* p, const SizeClass& c, const GsCall& g, cudaStream_t
       a.illum[k] = p->illum.empty() ? nullptr : p->illum[item];
     }
     a.mix = g.mix;
+    a.hio = g.hio ? c.hio : nullptr;
+    a.beta = g.beta;
     // field layout: single-plane runs tile the field in column strips when the row length allows
     // (contiguous strips for the column pass), else row-major
     const bool tiled = P == 1 && c.tile > 0;
@@ -816,7 +821,7 @@ hg_status gs_class(hg_plan* p, const SizeClass& c, const GsCall& g, cudaStream_t
       continue;
     }
     if (g.mix > 0.f) {
-      // MRAF: the signal region's target energy, for the absolute scale of m A_s
+      // MRAF / HIO: the signal region's target energy, for the absolute scale of m A_s
       const dim3 genergy(strips, nb), gfin(1, nb);
       if ((s = launch(p, K_AMP_ENERGY, (const void*)&k_amp_energy, genergy, 256, 0, a, st)) != HG_OK) return s;
       if ((s = launch(p, K_FINALIZE, (const void*)&hg::k_finalize<2>, gfin, 32, 0, a, st)) != HG_OK) return s;
@@ -932,6 +937,60 @@ hg_status run_maybe_graph(hg_plan* p, const std::vector<uintptr_t>& key,
   return HG_OK;
 }
 
+// MRAF and HIO: GS with a signal region (the rest of the replay plane is the noise region).
+hg_status region_run(hg_plan* p, const char* name, const float* const* target_amp,
+                     const uint8_t* const* signal_mask, float mix, bool hio, float beta,
+                     const float* const* init_phase, uint64_t seed, int32_t n_iter, float* const* phase_out,
+                     uint8_t* const* level_out, float* nmse_out, void* stream) {
+  if (!p) return fail(HG_ERR_INVALID_ARG, "plan is NULL");
+  if (p->P != 1) return fail(HG_ERR_INVALID_ARG, "%s needs a single-plane plan", name);
+  if (!p->illum.empty()) return fail(HG_ERR_INVALID_ARG, "%s does not take an illumination profile", name);
+  if (n_iter < 0 || n_iter > 1000000) return fail(HG_ERR_INVALID_ARG, "n_iter must be 0..1000000");
+  if (!target_amp) return fail(HG_ERR_INVALID_ARG, "target_amp is NULL");
+  if (level_out && p->levels == 0) {
+    for (int i = 0; i < p->n_items; ++i)
+      if (level_out[i]) return fail(HG_ERR_INVALID_ARG, "level_out needs a quantised plan");
+  }
+  DeviceGuard g(p->device);
+  if (!g.ok) return fail(HG_ERR_CUDA, "cannot select device %d", p->device);
+  hg_status s;
+  for (int i = 0; i < p->n_items; ++i) {
+    const size_t px = (size_t)p->H[i] * p->W[i];
+    if ((s = check_ptr(p, target_amp[i], px * 4, 4, "target_amp", i)) != HG_OK) return s;
+    if (signal_mask && signal_mask[i] && (s = check_ptr(p, signal_mask[i], px, 1, "signal_mask", i)) != HG_OK)
+      return s;
+    if (init_phase && init_phase[i] && (s = check_ptr(p, init_phase[i], px * 4, 4, "init_phase", i)) != HG_OK)
+      return s;
+    if (phase_out && phase_out[i] && (s = check_ptr(p, phase_out[i], px * 4, 4, "phase_out", i)) != HG_OK) return s;
+    if (level_out && level_out[i] && (s = check_ptr(p, level_out[i], px, 1, "level_out", i)) != HG_OK) return s;
+  }
+  if (nmse_out && (s = check_ptr(p, nmse_out, (size_t)p->n_items * (n_iter + 1) * 4, 4, "nmse_out", 0)) != HG_OK)
+    return s;
+  if (hio)
+    for (SizeClass& c : p->classes)  // sized for any strip width, like the target tiles
+      if (!c.hio && (s = p->alloc(&c.hio, c.items.size() * c.max_strip_cols() * c.H, "HIO input buffer")) != HG_OK)
+        return s;
+  GsCall call{target_amp, init_phase, seed, n_iter, phase_out, level_out, nmse_out};
+  call.mask = signal_mask;
+  call.mix = mix;
+  call.hio = hio;
+  call.beta = beta;
+  uint32_t bits[2];
+  std::memcpy(&bits[0], &mix, sizeof mix);
+  std::memcpy(&bits[1], &beta, sizeof beta);
+  std::vector<uintptr_t> key{(uintptr_t)(hio ? 4 : 3), (uintptr_t)n_iter, (uintptr_t)seed, (uintptr_t)nmse_out,
+                             (uintptr_t)bits[0], (uintptr_t)bits[1]};
+  if (p->graph)
+    for (int i = 0; i < p->n_items; ++i) {
+      key.push_back((uintptr_t)target_amp[i]);
+      key.push_back((uintptr_t)(signal_mask ? signal_mask[i] : nullptr));
+      key.push_back((uintptr_t)(init_phase ? init_phase[i] : nullptr));
+      key.push_back((uintptr_t)(phase_out ? phase_out[i] : nullptr));
+      key.push_back((uintptr_t)(level_out ? level_out[i] : nullptr));
+    }
+  return run_maybe_graph(p, key, [&](cudaStream_t q) { return gs_enqueue(p, call, q); }, (cudaStream_t)stream);
+}
+
 }  // namespace
 
 extern "C" {
@@ -995,46 +1054,17 @@ hg_status hg_plan_set_illumination(hg_plan* p, const float* const* illum_amp) {
 hg_status hg_mraf_run(hg_plan* p, const float* const* target_amp, const uint8_t* const* signal_mask, float mix,
                       const float* const* init_phase, uint64_t seed, int32_t n_iter, float* const* phase_out,
                       uint8_t* const* level_out, float* nmse_out, void* stream) {
-  if (!p) return fail(HG_ERR_INVALID_ARG, "plan is NULL");
-  if (p->P != 1) return fail(HG_ERR_INVALID_ARG, "MRAF needs a single-plane plan");
-  if (!p->illum.empty()) return fail(HG_ERR_INVALID_ARG, "MRAF does not take an illumination profile");
   if (!(mix > 0.f && mix <= 1.f)) return fail(HG_ERR_INVALID_ARG, "mix must be in (0, 1]");
-  if (n_iter < 0 || n_iter > 1000000) return fail(HG_ERR_INVALID_ARG, "n_iter must be 0..1000000");
-  if (!target_amp) return fail(HG_ERR_INVALID_ARG, "target_amp is NULL");
-  if (level_out && p->levels == 0) {
-    for (int i = 0; i < p->n_items; ++i)
-      if (level_out[i]) return fail(HG_ERR_INVALID_ARG, "level_out needs a quantised plan");
-  }
-  DeviceGuard g(p->device);
-  if (!g.ok) return fail(HG_ERR_CUDA, "cannot select device %d", p->device);
-  hg_status s;
-  for (int i = 0; i < p->n_items; ++i) {
-    const size_t px = (size_t)p->H[i] * p->W[i];
-    if ((s = check_ptr(p, target_amp[i], px * 4, 4, "target_amp", i)) != HG_OK) return s;
-    if (signal_mask && signal_mask[i] && (s = check_ptr(p, signal_mask[i], px, 1, "signal_mask", i)) != HG_OK)
-      return s;
-    if (init_phase && init_phase[i] && (s = check_ptr(p, init_phase[i], px * 4, 4, "init_phase", i)) != HG_OK)
-      return s;
-    if (phase_out && phase_out[i] && (s = check_ptr(p, phase_out[i], px * 4, 4, "phase_out", i)) != HG_OK) return s;
-    if (level_out && level_out[i] && (s = check_ptr(p, level_out[i], px, 1, "level_out", i)) != HG_OK) return s;
-  }
-  if (nmse_out && (s = check_ptr(p, nmse_out, (size_t)p->n_items * (n_iter + 1) * 4, 4, "nmse_out", 0)) != HG_OK)
-    return s;
-  GsCall call{target_amp, init_phase, seed, n_iter, phase_out, level_out, nmse_out};
-  call.mask = signal_mask;
-  call.mix = mix;
-  uint32_t mix_bits;
-  std::memcpy(&mix_bits, &mix, sizeof mix_bits);
-  std::vector<uintptr_t> key{3, (uintptr_t)n_iter, (uintptr_t)seed, (uintptr_t)nmse_out, (uintptr_t)mix_bits};
-  if (p->graph)
-    for (int i = 0; i < p->n_items; ++i) {
-      key.push_back((uintptr_t)target_amp[i]);
-      key.push_back((uintptr_t)(signal_mask ? signal_mask[i] : nullptr));
-      key.push_back((uintptr_t)(init_phase ? init_phase[i] : nullptr));
-      key.push_back((uintptr_t)(phase_out ? phase_out[i] : nullptr));
-      key.push_back((uintptr_t)(level_out ? level_out[i] : nullptr));
-    }
-  return run_maybe_graph(p, key, [&](cudaStream_t q) { return gs_enqueue(p, call, q); }, (cudaStream_t)stream);
+  return region_run(p, "MRAF", target_amp, signal_mask, mix, false, 0.f, init_phase, seed, n_iter, phase_out,
+                    level_out, nmse_out, stream);
+}
+
+hg_status hg_hio_run(hg_plan* p, const float* const* target_amp, const uint8_t* const* signal_mask, float beta,
+                     const float* const* init_phase, uint64_t seed, int32_t n_iter, float* const* phase_out,
+                     uint8_t* const* level_out, float* nmse_out, void* stream) {
+  if (!(beta > 0.f && beta <= 2.f)) return fail(HG_ERR_INVALID_ARG, "beta must be in (0, 2]");
+  return region_run(p, "HIO", target_amp, signal_mask, 1.f, true, beta, init_phase, seed, n_iter, phase_out,
+                    level_out, nmse_out, stream);
 }
 
 // ---------------------------------------------------------------- autotuner

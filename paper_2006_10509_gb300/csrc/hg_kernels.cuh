@@ -186,6 +186,10 @@ struct PassArgs {
   // the mixing parameter m; the target copy marks noise-region pixels with -1
   const uint8_t* mask[kMaxBatch];
   float mix;
+  // HIO (with mix = 1): the replay-plane input X on the noise region, [slot][strip][H][C] like the
+  // target tiles, in the unnormalised forward transform's scale; nullptr for MRAF / GS
+  float2* hio;
+  float beta;              // HIO feedback: X' = X - beta Y on the noise region
   const float* illum[kMaxBatch];  // GS: SLM illumination amplitude [H][W] per item (nullptr: uniform)
   float2* partials;        // class partial sums (hi, lo): (slot, plane) at partials + (slot P + p) 3 col_blocks
   float* nmse;             // nmse_out of the run (device) or nullptr
@@ -578,7 +582,9 @@ __global__ void __launch_bounds__(RowCfg<W>::NT) k_row_fft(const __grid_constant
 // amplitude replacement R' = A R / |R| -> inverse column FFTs.  With REPLACE = false only the NMSE
 // is taken (last iteration) and the field is not written.  CT > 0: the field is tiled in column
 // strips of width CT, each CTA's strip one contiguous block; CT = 0: row-major.  EXT instances
-// also take MRAF's mixed regions (the plain ones stay free of its per-pixel test).
+// also take the signal / noise regions of MRAF and HIO (the plain ones stay free of the per-pixel
+// test).  HIO keeps its noise-region input X between passes: on the signal region X' = A_s Y / |Y|
+// is the replacement itself, so X is stored for the noise region only.
 template <int H, bool REPLACE, int CT, bool EXT = false>
 __global__ void __launch_bounds__(ColCfg<H, CT>::NT, ColCfg<H, CT>::MINB)
     k_col_gs(const __grid_constant__ PassArgs a) {
@@ -608,6 +614,7 @@ __global__ void __launch_bounds__(ColCfg<H, CT>::NT, ColCfg<H, CT>::MINB)
   const float amp_scale = mraf ? a.mix * (float)H * (float)W * esc : esc;
   // tiled: this strip is one contiguous [H][C] block
   float2* fs = TILED ? f + (size_t)blockIdx.x * H * K::C : f;
+  float2* hx = EXT && a.hio ? a.hio + (((size_t)slot * P + p) * gridDim.x + blockIdx.x) * H * K::C : nullptr;
   float2 v[K::V];
   for_each_slot<G, K::RB>(t, [&](int s, int b, int n) {
     const int col = col0 + b;
@@ -623,8 +630,18 @@ __global__ void __launch_bounds__(ColCfg<H, CT>::NT, ColCfg<H, CT>::MINB)
   for_each_slot<G, RLast<typename K::Fwd>::value>(t, [&](int s, int b, int n) {
     const float2 r = v[s];
     const float amp = ts[n * K::C + b];
-    if (mraf && amp < 0.f) {  // MRAF noise region: R' = (1 - m) R, outside the ROI NMSE
-      if (REPLACE) v[s] = c_scale(r, 1.f - a.mix);
+    if (mraf && amp < 0.f) {  // noise region, outside the ROI NMSE
+      if (REPLACE) {
+        if (a.hio) {  // HIO: X' = X - beta Y, with X_0 = Y_0
+          float2* xp = hx + n * K::C + b;
+          const float2 x0 = a.iter == 0 ? r : __ldcg(xp);
+          const float2 xn = make_float2(fmaf(-a.beta, r.x, x0.x), fmaf(-a.beta, r.y, x0.y));
+          __stcg(xp, xn);
+          v[s] = xn;
+        } else {  // MRAF: R' = (1 - m) R
+          v[s] = c_scale(r, 1.f - a.mix);
+        }
+      }
       return;
     }
     const float i2 = fmaf(r.x, r.x, r.y * r.y);
