@@ -73,11 +73,18 @@ typedef struct {
   int32_t n_planes;        /* replay planes P >= 1 (Fourier: must be 1) */
   const double* z_m;       /* Fresnel: P propagation distances (> 0); may be NULL for Fourier */
   int32_t quant_levels;    /* 0 continuous phase; 2 binary {0, pi}; N in 3..256 N-level */
-  uint32_t flags;          /* 0 or HG_PLAN_AUTOTUNE */
+  uint32_t flags;          /* 0, or HG_PLAN_AUTOTUNE and / or HG_TARGET_CENTRED */
 } hg_plan_desc;
 
 /* hg_plan_create runs hg_plan_autotune before returning. */
 #define HG_PLAN_AUTOTUNE 1u
+/* Targets (hg_gs_run, hg_mraf_run, hg_hio_run, hg_ospr_run amplitudes, gradient-descent target
+ * intensities) and MRAF / HIO signal masks are given in display order, with the zero frequency at
+ * row H/2, column W/2 (integer halves): the plan reads pixel (i, j) of the FFT-ordered replay plane
+ * from ((i + H/2) mod H, (j + W/2) mod W) of the caller's array (numpy's ifftshift), in the pass
+ * that copies targets into the plan, so the loops run at the same speed.  Holograms, NMSE and
+ * gradients stay in the SLM's own pixel order; hg_propagate is not affected. */
+#define HG_TARGET_CENTRED 2u
 
 /*
  * Fresnel model (single-FFT, reading of the paper's "Fresnel" keyword): SLM pixel (i, j) at

@@ -182,6 +182,7 @@ struct hg_plan {
   std::vector<size_t> class_order;  // size classes, smallest first
   unsigned long long* stamps = nullptr;  // [1 + classes]: run start, end of each class (%globaltimer)
   bool graph = false;
+  bool centred = false;             // HG_TARGET_CENTRED: targets in display order
   bool capturing = false;           // enqueueing into a graph capture
   cudaStream_t cap = nullptr;       // capture stream of graph mode
   // graph mode keeps one executable graph per timing state: [1] also records a pair of events
@@ -405,13 +406,15 @@ void fill_common(const hg_plan* p, const SizeClass& c, int plane, hg::PassArgs& 
     a.cyp[q] = p->propagation == HG_FRESNEL ? c.cy[q] : nullptr;
   }
   a.stats = c.stats;
+  a.centred = p->centred ? 1 : 0;
 }
 
 }  // namespace
 
 // Re-lays the targets out per column strip for the GS column passes: strip t of (item, plane) holds
 // [H][C] contiguous (zero past W), so a column pass streams its strip with contiguous copies instead
-// of C-float pieces of every row.  blockIdx.x = strip, blockIdx.y = item * P + plane.
+// of C-float pieces of every row; targets and masks given in display order are ifftshifted on the
+// way.  blockIdx.x = strip, blockIdx.y = item * P + plane.
 __global__ void k_tile_target(const __grid_constant__ hg::PassArgs a, int C, float* ttile) {
   const int P = a.n_planes > 1 ? a.n_planes : 1;
   const int k = blockIdx.y / P, p = blockIdx.y % P;
@@ -421,8 +424,12 @@ __global__ void k_tile_target(const __grid_constant__ hg::PassArgs a, int C, flo
   const uint8_t* mask = a.mix > 0.f ? a.mask[k] : nullptr;  // MRAF: -1 marks the noise region
   for (int i = threadIdx.x; i < H * C; i += blockDim.x) {
     const int n = i / C, b = i % C;
-    const size_t px = (size_t)n * W + col0 + b;
-    dst[i] = col0 + b < W ? ((mask && !__ldg(&mask[px])) ? -1.f : __ldg(&A[px])) : 0.f;
+    if (col0 + b >= W) {
+      dst[i] = 0.f;
+      continue;
+    }
+    const size_t px = hg::target_index(a, n, col0 + b);  // display-order targets: ifftshift here
+    dst[i] = (mask && !__ldg(&mask[px])) ? -1.f : __ldg(&A[px]);
   }
 }
 
@@ -544,7 +551,8 @@ hg_status hg_plan_create(const hg_plan_desc* d, hg_plan** out) {
     return fail(HG_ERR_INVALID_ARG, "Fourier plans have exactly one plane");
   if (d->quant_levels < 0 || d->quant_levels == 1 || d->quant_levels > kMaxLevels)
     return fail(HG_ERR_INVALID_ARG, "quant_levels must be 0 or 2..%d", kMaxLevels);
-  if (d->flags & ~HG_PLAN_AUTOTUNE) return fail(HG_ERR_INVALID_ARG, "unknown flags 0x%x", d->flags);
+  if (d->flags & ~(HG_PLAN_AUTOTUNE | HG_TARGET_CENTRED))
+    return fail(HG_ERR_INVALID_ARG, "unknown flags 0x%x", d->flags);
   if (d->propagation == HG_FRESNEL) {
     if (!(d->wavelength_m > 0) || !(d->pitch_m > 0) || !std::isfinite(d->wavelength_m) || !std::isfinite(d->pitch_m))
       return fail(HG_ERR_INVALID_ARG, "Fresnel plans need wavelength_m > 0 and pitch_m > 0");
@@ -578,6 +586,7 @@ hg_status hg_plan_create(const hg_plan_desc* d, hg_plan** out) {
   p->P = d->n_planes;
   if (d->propagation == HG_FRESNEL) p->z.assign(d->z_m, d->z_m + d->n_planes);
   p->levels = d->quant_levels;
+  p->centred = (d->flags & HG_TARGET_CENTRED) != 0;
 
   // size classes
   p->item_class.resize(p->n_items);

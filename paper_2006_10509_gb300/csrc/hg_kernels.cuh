@@ -190,6 +190,7 @@ struct PassArgs {
   // target tiles, in the unnormalised forward transform's scale; nullptr for MRAF / GS
   float2* hio;
   float beta;              // HIO feedback: X' = X - beta Y on the noise region
+  int centred;             // targets (and signal masks) in display order: DC at (H/2, W/2)
   const float* illum[kMaxBatch];  // GS: SLM illumination amplitude [H][W] per item (nullptr: uniform)
   float2* partials;        // class partial sums (hi, lo): (slot, plane) at partials + (slot P + p) 3 col_blocks
   float* nmse;             // nmse_out of the run (device) or nullptr
@@ -574,6 +575,18 @@ __global__ void __launch_bounds__(RowCfg<W>::NT) k_row_fft(const __grid_constant
     const int row = row0 + b;
     if (row < H) dst[(size_t)row * W + n] = v[s];
   });
+}
+
+// Offset of replay-plane pixel (n, col) (FFT order) in a caller's target: the same offset, or for
+// targets in display order (DC at (H/2, W/2)) that of the ifftshifted pixel.
+__device__ __forceinline__ size_t target_index(const PassArgs& a, int n, int col) {
+  if (a.centred) {
+    n += a.H / 2;
+    n -= n >= a.H ? a.H : 0;
+    col += a.W / 2;
+    col -= col >= a.W ? a.W : 0;
+  }
+  return (size_t)n * a.W + col;
 }
 
 // ---------------------------------------------------------------- column passes
@@ -1009,7 +1022,7 @@ __global__ void __launch_bounds__(ColCfg<H>::NT, ColCfg<H>::MINB) k_col_gd(const
       if (col < W) {
         const float2 u = v[s];
         const float i2 = fmaf(u.x, u.x, u.y * u.y);
-        const float tt = __ldg(&T[(size_t)n * W + col]);
+        const float tt = __ldg(&T[target_index(a, n, col)]);
         s_it = fmaf(i2, tt, s_it);
         s_ii = fmaf(i2, i2, s_ii);
         s_tt = fmaf(tt, tt, s_tt);
@@ -1026,7 +1039,7 @@ __global__ void __launch_bounds__(ColCfg<H>::NT, ColCfg<H>::MINB) k_col_gd(const
       if (col < W) {
         const float2 u = v[s];
         const float i2 = fmaf(u.x, u.x, u.y * u.y);
-        const float tt = __ldg(&T[(size_t)n * W + col]);
+        const float tt = __ldg(&T[target_index(a, n, col)]);
         gi = c_scale(u, coef * fmaf(su, i2, -tt));
       }
       v[s] = gi;

@@ -58,7 +58,7 @@ def test_status_strings_and_lengths(hg):
         (dict(heights=[64], widths=[64], propagation=1, wavelength_m=0.0, pitch_m=8e-6, z_m=[0.1]), 1),
         (dict(heights=[64], widths=[64], propagation=1, wavelength_m=5e-7, pitch_m=8e-6, z_m=[-0.1]), 1),
         (dict(heights=[64], widths=[64], z_m=[0.1, 0.2]), 1),
-        (dict(heights=[64], widths=[64], flags=3), 1),
+        (dict(heights=[64], widths=[64], flags=4), 1),
     ],
 )
 def test_create_rejects_bad_descriptors(hg, kwargs, status):
