@@ -78,6 +78,8 @@ typedef struct {
 
 /* hg_plan_create runs hg_plan_autotune before returning. */
 #define HG_PLAN_AUTOTUNE 1u
+/* Strip width that selects the whole-run cluster kernel (hg_plan_set_strip_width). */
+#define HG_STRIP_CLUSTER (-1)
 /* Targets (hg_gs_run, hg_mraf_run, hg_hio_run, hg_ospr_run amplitudes, gradient-descent target
  * intensities) and MRAF / HIO signal masks are given in display order, with the zero frequency at
  * row H/2, column W/2 (integer halves): the plan reads pixel (i, j) of the FFT-ordered replay plane
@@ -294,6 +296,13 @@ HG_API hg_status hg_plan_set_graph(hg_plan* plan, int32_t enabled);
  * hg_plan_strip_width returns the width in use for an item's size class (0: row-major field);
  * hg_plan_set_strip_width sets it by hand (synchronises the device, drops captured graphs;
  * HG_ERR_INVALID_ARG for a width the class does not allow).
+ * Width -1 (HG_STRIP_CLUSTER), available for square classes of 64, 128 or 256 pixels on a
+ * single-plane plan and the default for such a class of one item: hg_gs_run runs the whole loop of each item in one
+ * launch, one thread-block cluster (16 CTAs where the device runs clusters that large, else 8)
+ * per item with the field held in the cluster's shared memory; the arithmetic per pixel is that
+ * of the two-pass kernels, only the NMSE partial sums are grouped differently.  MRAF, HIO and
+ * illuminated runs of such a class use the default strip width; the autotuner includes -1 among
+ * the candidates.
  */
 HG_API hg_status hg_plan_autotune(hg_plan* plan, void* stream);
 HG_API hg_status hg_plan_strip_width(const hg_plan* plan, int32_t item, int32_t* width_out);

@@ -25,7 +25,7 @@ __all__ = [
     "hg_plan_launch_count", "hg_gs_run_noalloc", "hg_ospr_run", "hg_gd_step", "hg_gd_forward",
     "hg_gd_backward", "hologram_loss", "hg_plan_set_graph", "hg_plan_item_latency", "hg_plan_autotune",
     "hg_plan_strip_width", "hg_plan_set_strip_width", "HG_PLAN_AUTOTUNE", "hg_mraf_run",
-    "hg_plan_set_illumination", "hg_hio_run", "HG_TARGET_CENTRED",
+    "hg_plan_set_illumination", "hg_hio_run", "HG_TARGET_CENTRED", "HG_STRIP_CLUSTER",
 ]
 
 HG_OK, HG_ERR_INVALID_ARG, HG_ERR_UNSUPPORTED_SIZE, HG_ERR_OUT_OF_MEMORY = 0, 1, 2, 3
@@ -33,6 +33,7 @@ HG_ERR_CUDA, HG_ERR_TIMEOUT, HG_ERR_INTERNAL = 4, 5, 6
 HG_FOURIER, HG_FRESNEL = 0, 1
 HG_PLAN_AUTOTUNE = 1  # plan flag: autotune the strip widths at creation
 HG_TARGET_CENTRED = 2  # plan flag: targets and signal masks in display order (DC at H/2, W/2)
+HG_STRIP_CLUSTER = -1  # strip width: the whole GS run in one thread-block cluster per item
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB = None

@@ -99,12 +99,12 @@ constexpr int kMaxItems = 256;
 enum Kind {
   K_ROW_INIT = 0, K_ROW_GS, K_COL_GS, K_COL_NMSE, K_ROW_FFT, K_COL_FFT, K_ROW_OSPR, K_COL_OSPR,
   K_ROW_MP_INIT, K_ROW_MP, K_ROW_GD_FWD, K_COL_GD_FWD, K_COL_GD_BWD, K_ROW_GD_BWD, K_AMP_ENERGY, K_FINALIZE,
-  K_TILE_TARGET, K_NUM_KINDS
+  K_TILE_TARGET, K_GS_CLUSTER, K_NUM_KINDS
 };
 const char* const kKindNames[K_NUM_KINDS] = {"row_init",   "row_gs",     "col_gs",     "col_nmse",  "row_fft",
                                              "col_fft",    "row_ospr",   "col_ospr",   "row_mp_init", "row_mp",
                                              "row_gd_fwd", "col_gd_fwd", "col_gd_bwd", "row_gd_bwd",
-                                             "amp_energy", "finalize", "tile_target"};
+                                             "amp_energy", "finalize", "tile_target", "gs_cluster"};
 constexpr int kMaxLevels = 256;
 
 struct SizeClass {
@@ -121,17 +121,22 @@ struct SizeClass {
   std::vector<float2*> cx, cy;   // per plane (Fresnel)
   int row_blocks() const { return (H + rk->rows - 1) / rk->rows; }
   int col_blocks() const { return (W + ck->cols - 1) / ck->cols; }    // strips on a row-major field
-  // strip width of the tiled GS field (0: single-plane GS keeps the field row-major); the default
-  // rule at plan creation, or the autotuner's choice
+  // strip width of the tiled GS field (0: single-plane GS keeps the field row-major; -1: GS runs
+  // in the whole-run cluster kernel); the default rule at plan creation, or the autotuner's choice
   int tile = 0;
-  int col_blocks_t() const { return (W + tile - 1) / tile; }  // strips of the tiled GS field
   // sizes covering any strip width (the narrowest tiled one is 2): partial sums per strip, and the
   // strips x H x width target copies
   size_t max_strips() const { return (size_t)std::max(col_blocks(), (W + 1) / 2); }
   size_t max_strip_cols() const {
     return std::max((size_t)col_blocks() * ck->cols, (size_t)(W + 15) / 16 * 16);
   }
-  // whether the GS field can be tiled in strips of width w here (kernels exist, rows tile evenly)
+  // GS with the whole run in one thread-block cluster per item (strip width -1): CTAs per cluster
+  // (0: not available for this class), kernel, threads, shared memory
+  int cl = 0;
+  const void* cl_fn = nullptr;
+  int cl_nt = 0, cl_smem = 0;
+  // whether the GS field can be tiled in strips of width w here (kernels exist, rows tile evenly);
+  // w = -1: the whole-run cluster kernel
   bool tileable(int w, int planes) const;
 };
 
@@ -139,6 +144,7 @@ struct SizeClass {
 int tile_index(int cols) { return cols == 2 ? 0 : (cols == 4 ? 1 : (cols == 8 ? 2 : 3)); }
 
 bool SizeClass::tileable(int w, int planes) const {
+  if (w == -1) return planes == 1 && cl > 0;
   if (planes != 1 || (w != 2 && w != 4 && w != 8 && w != 16) || W % w != 0) return false;
   const int ti = tile_index(w);
   return ck->tiled[ti].gs[0][0] != nullptr && rk->init_t[ti][0] != nullptr;
@@ -305,7 +311,7 @@ hg_status check_ptr(const hg_plan* p, const void* ptr, size_t bytes, size_t alig
 }
 
 hg_status launch(hg_plan* p, int kind, const void* fn, dim3 grid, int nt, int smem, const hg::PassArgs& a,
-                 cudaStream_t s, int extra_int = 0, float* extra_ptr = nullptr) {
+                 cudaStream_t s, int extra_int = 0, float* extra_ptr = nullptr, int cluster_x = 0) {
   void* args3[] = {(void*)&a, (void*)&extra_int, (void*)&extra_ptr};
   void** args = args3;  // kernels with one parameter read only the first entry
   cudaEvent_t ea = nullptr, eb = nullptr;
@@ -323,7 +329,21 @@ hg_status launch(hg_plan* p, int kind, const void* fn, dim3 grid, int nt, int sm
   const bool pdl = HG_PDL && !p->timing && !p->capturing &&
                    (kind == K_COL_GS || kind == K_ROW_GS || kind == K_COL_NMSE) &&
                    (int64_t)a.H * a.W * a.n_items <= (int64_t)2048 * 2048;
-  if (pdl) {
+  if (cluster_x > 0) {  // thread-block clusters of cluster_x CTAs along x
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(nt);
+    cfg.dynamicSmemBytes = (size_t)smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr{};
+    attr.id = cudaLaunchAttributeClusterDimension;
+    attr.val.clusterDim.x = (unsigned)cluster_x;
+    attr.val.clusterDim.y = 1;
+    attr.val.clusterDim.z = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelExC(&cfg, fn, args);
+  } else if (pdl) {
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = grid;
     cfg.blockDim = dim3(nt);
@@ -385,6 +405,39 @@ hg_status upload(hg_plan* p, T** dst, const std::vector<T>& v, const char* what)
   if (s != HG_OK) return s;
   HG_CUDA(cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice), what);
   return HG_OK;
+}
+
+// The whole-run cluster kernel of a square class: 16 CTAs per cluster where the device can run such
+// a cluster (a non-portable size), else 8; none for other shapes or lengths.
+void pick_cluster(SizeClass& c) {
+  c.cl = 0;
+  if (c.H != c.W) return;
+  for (int i = 1; i >= 0; --i) {
+    const void* fn = c.rk->gs_cluster[i];
+    if (!fn) continue;
+    const int cl = i ? 16 : 8;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(cl, 1);
+    cfg.blockDim = dim3(c.rk->nt_cluster[i]);
+    cfg.dynamicSmemBytes = (size_t)c.rk->smem_cluster[i];
+    cudaLaunchAttribute attr{};
+    attr.id = cudaLaunchAttributeClusterDimension;
+    attr.val.clusterDim.x = (unsigned)cl;
+    attr.val.clusterDim.y = 1;
+    attr.val.clusterDim.z = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, fn, &cfg) != cudaSuccess || n < 1) {
+      cudaGetLastError();  // not available: clear the error and try the smaller cluster
+      continue;
+    }
+    c.cl = cl;
+    c.cl_fn = fn;
+    c.cl_nt = c.rk->nt_cluster[i];
+    c.cl_smem = c.rk->smem_cluster[i];
+    return;
+  }
 }
 
 void fill_common(const hg_plan* p, const SizeClass& c, int plane, hg::PassArgs& a) {
@@ -615,7 +668,12 @@ hg_status hg_plan_create(const hg_plan_desc* d, hg_plan** out) {
     c.ck->set_attrs();
     const size_t n = c.items.size() * (size_t)p->P;
     if ((s = p->alloc(&c.field, n * c.H * c.W, "field workspace")) != HG_OK) return bail(s);
-    c.tile = c.tileable(c.ck->tile, p->P) ? c.ck->tile : 0;
+    pick_cluster(c);
+    // default: the whole-run cluster kernel for a class of one item where it exists (measured on
+    // GB300, 20 iterations: 64^2 112 against 160 us, 128^2 177 against 207, 256^2 222 against 224;
+    // with 16 items of 256^2 it takes twice as long as the two-pass kernels, whose launches then
+    // fill the GPU), else the measured strip width
+    c.tile = (c.items.size() == 1 && c.tileable(-1, p->P)) ? -1 : (c.tileable(c.ck->tile, p->P) ? c.ck->tile : 0);
     if ((s = p->alloc(&c.partials, n * 3 * c.max_strips(), "reduction scratch")) != HG_OK) return bail(s);
     if ((s = p->alloc(&c.stats, n * 4, "loss statistics")) != HG_OK) return bail(s);
     if ((s = p->alloc(&c.ttile, n * c.max_strip_cols() * c.H, "target tiles")) != HG_OK)
@@ -784,12 +842,29 @@ hg_status gs_class(hg_plan* p, const SizeClass& c, const GsCall& g, cudaStream_t
     a.mix = g.mix;
     a.hio = g.hio ? c.hio : nullptr;
     a.beta = g.beta;
+    bool lit = false;
+    for (int k = 0; k < nb; ++k) lit = lit || a.illum[k] != nullptr;
+    if (c.tile == -1 && P == 1 && g.mix == 0.f && !lit) {
+      // the whole run in one launch: one cluster per item, the field in the cluster's shared memory
+      for (int k = 0; k < nb; ++k) {
+        const int item = c.items[c0 + k];
+        a.phase_out[k] = phase_out ? phase_out[item] : nullptr;
+        a.level_out[k] = level_out ? level_out[item] : nullptr;
+      }
+      a.n_iter = n_iter;
+      if ((s = launch(p, K_GS_CLUSTER, c.cl_fn, dim3(c.cl, nb), c.cl_nt, c.cl_smem, a, st, 0, nullptr, c.cl)) !=
+          HG_OK)
+        return s;
+      continue;
+    }
     // field layout: single-plane runs tile the field in column strips when the row length allows
-    // (contiguous strips for the column pass), else row-major
-    const bool tiled = P == 1 && c.tile > 0;
-    const int ti = tiled ? tile_index(c.tile) : 0;
-    const int strip = tiled ? c.tile : c.ck->cols;
-    const int strips = tiled ? c.col_blocks_t() : c.col_blocks();
+    // (contiguous strips for the column pass), else row-major; MRAF, HIO and illuminated runs of a
+    // class set to the cluster kernel take the default strip width
+    const int width = c.tile == -1 ? (c.tileable(c.ck->tile, P) ? c.ck->tile : 0) : c.tile;
+    const bool tiled = P == 1 && width > 0;
+    const int ti = tiled ? tile_index(width) : 0;
+    const int strip = tiled ? width : c.ck->cols;
+    const int strips = tiled ? (c.W + width - 1) / width : c.col_blocks();
     a.col_blocks = strips;
     // targets re-laid out per column strip once per run (read by every column pass of the run)
     if ((s = launch(p, K_TILE_TARGET, (const void*)&k_tile_target, dim3(strips, nb * P), 256, 0, a, st, strip,
@@ -836,8 +911,6 @@ hg_status gs_class(hg_plan* p, const SizeClass& c, const GsCall& g, cudaStream_t
       if ((s = launch(p, K_FINALIZE, (const void*)&hg::k_finalize<2>, gfin, 32, 0, a, st)) != HG_OK) return s;
     }
     // extended kernels only when the run uses MRAF or an illumination profile
-    bool lit = false;
-    for (int k = 0; k < nb; ++k) lit = lit || a.illum[k] != nullptr;
     const int x = (g.mix > 0.f || lit) ? 1 : 0;
     const void* k_init = tiled ? c.rk->init_t[ti][x] : c.rk->init[x];
     const void* k_row[2] = {tiled ? c.rk->gs_t[ti][0][x] : c.rk->gs[0][x],
@@ -1091,6 +1164,7 @@ std::map<std::vector<int64_t>, int> g_tune_cache;
 
 static hg_status autotune_class(hg_plan* p, SizeClass& c, cudaStream_t st) {
   std::vector<int> cand;
+  if (c.tileable(-1, p->P)) cand.push_back(-1);  // whole run in one cluster per item
   for (int w : {2, 4, 8, 16})
     if (c.tileable(w, p->P)) cand.push_back(w);
   cand.push_back(0);  // row-major field

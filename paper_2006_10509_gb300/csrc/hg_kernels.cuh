@@ -14,6 +14,8 @@
 // propagation entry point.
 #pragma once
 
+#include <cooperative_groups.h>
+
 #include "hg_fft.cuh"
 
 namespace hg {
@@ -175,6 +177,7 @@ struct PassArgs {
   int finalize;            // row passes: 1 = first add up the preceding column pass's NMSE
   int fin_iter;            // nmse slot of that column pass
   int nmse_stride;         // floats between items in nmse_out (n_iter + 1)
+  int n_iter;              // whole-run kernels: GS iterations
   const float2* tw_row;    // per-stage twiddle tables of length W (TwBlob<W>)
   const float2* tw_col;    // per-stage twiddle tables of length H (TwBlob<H>)
   const float2* cx;        // Fresnel chirp along a row (W), nullptr for Fourier
@@ -1108,6 +1111,147 @@ __global__ void __launch_bounds__(RowCfg<W>::NT, RowCfg<W>::MINB) k_row_gd_bwd(c
       phi[px] = ph - a.lr * (m1 / a.bc1) / (sqrtf(v1 / a.bc2) + a.eps);
     }
   });
+}
+
+// ---------------------------------------------------------------- whole run in one cluster
+
+// GS for small holograms (N x N) with the whole run in one launch: one thread-block cluster of CL
+// CTAs per item, the field resident in the cluster's shared memory -- CTA r holds rows
+// [r N / CL, (r + 1) N / CL) -- so nothing but the target (once) and the outputs crosses HBM.  The
+// column phase of CTA r transforms columns [r N / CL, (r + 1) N / CL) of every CTA's rows, read
+// and written back through distributed shared memory; the row phase works on the CTA's own rows.
+// The arithmetic per element is that of the two-pass kernels (same radix plans, twiddles and
+// pointwise steps); only the NMSE partial sums are grouped per CTA.
+template <int N, int CL>
+struct ClusterCfg {
+  static constexpr int RL = N / CL;  // rows per CTA = columns per CTA in the column phase
+  using Fwd = typename PlanFor<N>::type;
+  using Inv = typename RRev<Fwd>::type;
+  static constexpr int NT = pick_threads<Fwd>(N, RL, value_budget(N), 1024);
+  using GR = Geo<N, RL, NT, false>;  // row tile: the CTA's RL rows
+  using GC = Geo<N, RL, NT, true>;   // column strip: RL columns of length N
+  static constexpr int V = hg_max(MaxV<GR, Fwd>::value, MaxV<GC, Fwd>::value);
+  static constexpr int XCH = hg_max(GR::SM_ELEMS, GC::SM_ELEMS);  // exchange float2 slots
+  static constexpr int FIELD = RL * N;                            // the CTA's rows, float2
+  static constexpr int PARTS = round_up(3 * CL, 2);               // rank 0: NMSE partials, float2
+  static constexpr int SMEM = (XCH + FIELD + PARTS) * 8 + N * RL * 4;  // + the target strip
+  static constexpr bool FEASIBLE = N % CL == 0 && RL >= 1 &&
+                                   RValues<Fwd>::max_values(N, RL, NT) <= value_budget(N) &&
+                                   SMEM <= 227 * 1024;
+};
+
+template <int N, int CL>
+__global__ void __launch_bounds__(ClusterCfg<N, CL>::NT, 1) k_gs_cluster(const __grid_constant__ PassArgs a) {
+  using K = ClusterCfg<N, CL>;
+  using GR = typename K::GR;
+  using GC = typename K::GC;
+  using Fwd = typename K::Fwd;
+  using Inv = typename K::Inv;
+  constexpr int RL = K::RL;
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  extern __shared__ __align__(16) float2 sm[];
+  float2* xs = sm;                                          // FFT exchange
+  float2* fld = sm + K::XCH;                                // this CTA's rows [RL][N]
+  float2* parts = fld + K::FIELD;                           // rank 0: [CL][3] (hi, lo) partials
+  float* ts = reinterpret_cast<float*>(parts + K::PARTS);   // target columns [N][RL] of this CTA
+  const int t = threadIdx.x, k = blockIdx.y;
+  const int rank = (int)cluster.block_rank();  // == blockIdx.x (gridDim.x == CL)
+  const int row0 = rank * RL, col0 = rank * RL;
+  const int n_iter = a.n_iter;
+  const float* A = a.target[k];
+  for (int i = t; i < N * RL; i += K::NT) ts[i] = __ldg(&A[target_index(a, i / RL, col0 + i % RL)]);
+  float2* part0 = cluster.map_shared_rank(parts, 0);
+  float* po = a.phase_out[k];
+  uint8_t* lo = a.level_out[k];
+  const float* ph = a.phase_in[k];
+
+  // h_0 on this CTA's rows (written out when there is no iteration), forward row FFTs
+  float2 v[K::V];
+  for_each_slot<GR, RFirst<Fwd>::value>(t, [&](int s, int b, int n) {
+    const int row = row0 + b;
+    const size_t p = (size_t)row * N + n;
+    float2 e;
+    if (ph) {
+      float sn, cs;
+      sincosf(__ldg(&ph[p]), &sn, &cs);
+      e = make_float2(cs, sn);
+    } else {
+      e = init_unit((uint32_t)p, a.seed, a.item_index[k]);
+    }
+    int q;
+    float2 h = slm_project(e, a.n_levels, a.lev, q);
+    if (n_iter == 0) {
+      if (po) po[p] = a.n_levels ? __ldg(&a.lev_phase[q]) : phase_0_2pi(h);
+      if (lo) lo[p] = (uint8_t)q;
+    }
+    if (a.cx) h = c_mul(h, c_mul(__ldg(&a.cx[n]), __ldg(&a.cy[row])));
+    v[s] = h;
+  });
+  FftRun<GR, false, 1, Fwd>::run(v, xs, t, a.tw_row);
+  for_each_slot<GR, RLast<Fwd>::value>(t, [&](int s, int b, int n) { fld[b * N + n] = v[s]; });
+  cluster.sync();
+
+  for (int it = 0;; ++it) {
+    const bool replace = it < n_iter;
+    // column phase: NMSE of h_it, and unless last, replacement and inverse column FFTs
+    for_each_slot<GC, RFirst<Fwd>::value>(t, [&](int s, int b, int n) {
+      const float2* src = cluster.map_shared_rank(fld, n / RL);
+      v[s] = src[(n % RL) * N + col0 + b];
+    });
+    FftRun<GC, false, 1, Fwd>::run(v, xs, t, a.tw_col);
+    float s_it = 0.f, s_ii = 0.f, s_tt = 0.f;
+    for_each_slot<GC, RLast<Fwd>::value>(t, [&](int s, int b, int n) {
+      const float2 r = v[s];
+      const float amp = ts[n * RL + b];
+      const float i2 = fmaf(r.x, r.x, r.y * r.y);
+      const float tt = amp * amp;
+      s_it = fmaf(i2, tt, s_it);
+      s_ii = fmaf(i2, i2, s_ii);
+      s_tt = fmaf(tt, tt, s_tt);
+      v[s] = i2 > 0.f ? c_scale(r, amp * rsqrtf(i2)) : make_float2(amp, 0.f);
+    });
+    block_partials(s_it, s_ii, s_tt, part0);
+    if (replace) {
+      FftRun<GC, true, 1, Inv>::run(v, xs, t, a.tw_col);
+      for_each_slot<GC, RLast<Inv>::value>(t, [&](int s, int b, int n) {
+        float2* dst = cluster.map_shared_rank(fld, n / RL);
+        dst[(n % RL) * N + col0 + b] = v[s];
+      });
+    }
+    cluster.sync();  // field and partials of the column phase in place
+    if (rank == 0 && t < 32) {
+      double tot[3];
+      sum_partials(parts, CL, tot);
+      if (t == 0 && a.nmse) a.nmse[(size_t)a.item_index[k] * a.nmse_stride + it] = (float)nmse_of(tot);
+    }
+    if (!replace) break;
+    // row phase on this CTA's rows: inverse row FFTs, SLM projection, forward row FFTs
+    for_each_slot<GR, RFirst<Inv>::value>(t, [&](int s, int b, int n) { v[s] = fld[b * N + n]; });
+    FftRun<GR, true, 1, Inv>::run(v, xs, t, a.tw_row);
+    const bool out = it == n_iter - 1;
+    for_each_slot<GR, RFirst<Fwd>::value>(t, [&](int s, int b, int n) {
+      const int row = row0 + b;
+      float2 g = v[s];
+      float2 c = make_float2(1.f, 0.f);
+      if (a.cx) {
+        c = c_mul(__ldg(&a.cx[n]), __ldg(&a.cy[row]));
+        g = c_mulc(g, c);
+      }
+      int q;
+      float2 h = slm_project(g, a.n_levels, a.lev, q);
+      if (out) {
+        const size_t p = (size_t)row * N + n;
+        if (po) po[p] = a.n_levels ? __ldg(&a.lev_phase[q]) : phase_0_2pi(h);
+        if (lo) lo[p] = (uint8_t)q;
+      }
+      if (a.cx) h = c_mul(h, c);
+      v[s] = h;
+    });
+    FftRun<GR, false, 1, Fwd>::run(v, xs, t, a.tw_row);
+    for_each_slot<GR, RLast<Fwd>::value>(t, [&](int s, int b, int n) { fld[b * N + n] = v[s]; });
+    cluster.sync();  // rows in place before the next column phase reads them
+  }
 }
 
 }  // namespace hg

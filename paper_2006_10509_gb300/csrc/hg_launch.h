@@ -31,6 +31,10 @@ struct RowKernels {
   const void* mp_init[2];   // k_row_mp_init<PROJECT = false (gradient descent) / true (GS)>
   const void* mp[2];        // k_row_mp<OUT = false / true>
   const void* gd_bwd;       // k_row_gd_bwd
+  // GS with the whole run in one thread-block cluster per N x N item (k_gs_cluster; nullptr where
+  // not instantiated): [0] clusters of 8 CTAs, [1] of 16
+  const void* gs_cluster[2];
+  int nt_cluster[2], smem_cluster[2];
   void (*set_attrs)();      // raises the dynamic shared-memory limit on the current device
   TwiddleLayout tw;         // twiddle tables of length W
 };

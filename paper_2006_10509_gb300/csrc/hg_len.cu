@@ -58,6 +58,27 @@ void set_tiled_attrs() {
   }
 }
 
+// whole-run cluster kernels for the small square sizes (the field of one item fits the shared
+// memory of one cluster)
+constexpr bool cluster_len(int n) { return n == 64 || n == 128 || n == 256; }
+
+template <int N, int CL>
+void fill_cluster(RowKernels& r, int i) {
+  if constexpr (cluster_len(N) && ClusterCfg<N, CL>::FEASIBLE) {
+    r.gs_cluster[i] = (const void*)&k_gs_cluster<N, CL>;
+    r.nt_cluster[i] = ClusterCfg<N, CL>::NT;
+    r.smem_cluster[i] = ClusterCfg<N, CL>::SMEM;
+  }
+}
+
+template <int N, int CL>
+void set_cluster_attrs() {
+  if constexpr (cluster_len(N) && ClusterCfg<N, CL>::FEASIBLE) {
+    allow_smem(&k_gs_cluster<N, CL>, ClusterCfg<N, CL>::SMEM);
+    if (CL > 8) cudaFuncSetAttribute((const void*)&k_gs_cluster<N, CL>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  }
+}
+
 template <int N>
 RowKernels make_row() {
   using K = RowCfg<N>;
@@ -87,6 +108,8 @@ RowKernels make_row() {
   r.mp[0] = (const void*)&k_row_mp<N, false>;
   r.mp[1] = (const void*)&k_row_mp<N, true>;
   r.gd_bwd = (const void*)&k_row_gd_bwd<N>;
+  fill_cluster<N, 8>(r, 0);
+  fill_cluster<N, 16>(r, 1);
   r.tw = make_tw<N>();
   return r;
 }
@@ -167,6 +190,8 @@ void set_row_attrs(const RowKernels& r) {
   allow_smem(&k_row_mp<HG_LEN, false>, r.smem);
   allow_smem(&k_row_mp<HG_LEN, true>, r.smem);
   allow_smem(&k_row_gd_bwd<HG_LEN>, r.smem);
+  set_cluster_attrs<HG_LEN, 8>();
+  set_cluster_attrs<HG_LEN, 16>();
 }
 
 void set_col_attrs(const ColKernels& c) {

@@ -1,7 +1,8 @@
 """Strip widths of the tiled GS field and the autotuner that picks them.
 
-Every width a size class allows (2, 4, 8 or 16 columns, or the row-major field) runs the same FFTs
-on the same values, so quantised levels and phases must be bitwise equal across widths; only the
+Every width a size class allows (2, 4, 8 or 16 columns, the row-major field, or -1, the whole run in
+one thread-block cluster per item) runs the same FFTs on the same values, so quantised levels and
+phases must be bitwise equal across widths; only the
 grouping of the NMSE partial sums changes, so NMSE agrees to float rounding.  The autotuner must
 pick one of the allowed widths and leave results unchanged.
 """
@@ -42,7 +43,7 @@ def test_every_strip_width_gives_the_same_hologram(h, w, levels):
     with hg.Plan([h], [w], quant_levels=levels) as plan:
         ref = _run(hg, dev, plan, a, p, 5, levels)
         tried = [plan.strip_width(0)]
-        for width in (0, 2, 4, 8, 16):
+        for width in (-1, 0, 2, 4, 8, 16):
             try:
                 plan.set_strip_width(0, width)
             except hg.HologenError as e:
@@ -67,7 +68,7 @@ def test_autotune_picks_an_allowed_width_and_keeps_results():
         defaults = [plan.strip_width(i) for i in range(len(sizes))]
         plan.autotune()
         tuned = [plan.strip_width(i) for i in range(len(sizes))]
-    assert all(t in (0, 2, 4, 8, 16) for t in tuned)
+    assert all(t in (-1, 0, 2, 4, 8, 16) for t in tuned)
     # the flag runs the same tuning at creation (cached choices: identical)
     with hg.Plan([s[0] for s in sizes], [s[1] for s in sizes], quant_levels=4, flags=hg.HG_PLAN_AUTOTUNE) as plan:
         assert [plan.strip_width(i) for i in range(len(sizes))] == tuned
