@@ -9,7 +9,7 @@ Fourier transform algorithms (HoloGenAlgGSCuda), One-Step Phase-Retrieval (HoloG
 Fourier and Fresnel holograms (keywords), an FFT handler (FFTHandlerCuda), a quantiser
 (QuantiserCuda), a normaliser and a randomiser -- but prints no equation for any of them.  Each
 module therefore writes out the published method the name refers to (Gerchberg & Saxton 1972;
-Fienup 1982; Cable, Buckley et al. 2004; Pasienski & DeMarco 2008; Goodman's single-FFT Fresnel
+Fienup 1982; Cable, Buckley et al. 2004; Pasienski & DeMarco 2008; Seldowitz, Allebach & Sweeney 1987; Goodman's single-FFT Fresnel
 transform; Kingma & Ba 2015; Salmon et al. 2011) in plain numpy float64, and every reading taken where the paper is silent is
 stated in the docstring of the function that takes it.
 
@@ -25,7 +25,9 @@ Modules:
   project   SLM-plane projections (continuous / N-level / binary) and amplitude replacement
   metrics   optimal-scale intensity NMSE
   gs        Gerchberg-Saxton (single plane) and averaged-projection multi-plane GS
-  mraf      mixed-region amplitude freedom (signal window, mixing m) and region-of-interest NMSE
+  mraf      mixed-region amplitude freedom (signal window, mixing m), hybrid input-output, and
+            region-of-interest NMSE
+  dbs       direct binary search with the single-pixel replay update
   philox    Philox4x32-10 counter-based generator
   ospr      One-Step Phase-Retrieval
   gd        gradient-descent (Wirtinger) loss, analytic gradient and Adam
