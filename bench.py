@@ -536,7 +536,10 @@ def run_config(args):
         nm = torch.zeros((nt, ns), dtype=torch.float32, device=dev)
         run = lambda: plan.ospr(ts, ns, 0, 3000, bits_out=bits, nmse_out=nm)  # noqa: E731
         units, unit, bpu = nt * ns, "subframes/s", 44 * h * wd
-    plan.autotune()  # GS strip widths (OSPR keeps its row-major field)
+    if args.strip_width is None:
+        plan.autotune()  # GS strip widths (OSPR keeps its row-major field)
+    else:
+        plan.set_strip_width(0, args.strip_width)
     width = plan.strip_width(0)
     plan.set_graph(True)
     for _ in range(args.warmup):
@@ -556,7 +559,7 @@ def run_config(args):
     line = {"workload": w, "value": units / (ms / 1e3), "unit": unit, "ms_per_run": ms,
             "alg_bytes_per_unit": bpu, "achieved_gb_s": gbs, "frac_of_hbm": gbs / peak, "peak_source": src,
             "final_nmse": nm.cpu().numpy()[:, -1].tolist()[:4], "steps": args.steps, "warmup": args.warmup,
-            "graph": True, "autotuned_strip_width": width}
+            "graph": True, ("strip_width" if args.strip_width is not None else "autotuned_strip_width"): width}
     plan.close()
     print(json.dumps(line))
 
@@ -656,6 +659,9 @@ def main():
                     help="gs2048: the headline line; batch: the mixed-size serving batch; "
                          "gd: gradient descent vs multi-plane GS, time to NMSE; gs256 / fresnel1024 / ospr: "
                          "the other single-GPU configurations; mraf2048 / hio2048: the MRAF and HIO variants of GS")
+    ap.add_argument("--strip-width", type=int, default=None,
+                    help="gs256 / fresnel1024 / mraf2048 / hio2048: use this strip width (-1: the whole run in "
+                         "one thread-block cluster) instead of the autotuner's choice")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
