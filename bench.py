@@ -527,6 +527,16 @@ def run_config(args):
         run = lambda: plan.hio([a], 0.7, n_iter, signal_mask=[mask], init_phase=[p0], nmse_out=nm)  # noqa: E731
         # GS's 36 B/px plus the stored input X read and written on the noise region
         units, unit, bpu = n_iter, "it/s", 36 * h * wd + 16 * (h * wd - (h // 4) * (wd // 4))
+    elif w == "dbs128":
+        h = wd = 128
+        n_sweeps = 2
+        a = torch.from_numpy(synth.blur_target(h, wd, SIGMA, seed=7001)).to(dev)
+        p0 = torch.from_numpy(synth.uniform_phase(h, wd, seed=7002)).to(dev)
+        plan = hg.Plan([h], [wd], quant_levels=2)
+        nm = torch.zeros((1, n_sweeps + 1), dtype=torch.float32, device=dev)
+        run = lambda: plan.dbs([a], n_sweeps, init_phase=[p0], nmse_out=nm)  # noqa: E731
+        # trial flips; the replay plane stays in registers, so no HBM bytes per trial
+        units, unit, bpu = n_sweeps * h * wd, "trial flips/s", 0
     else:
         h, wd, nt, ns = 1080, 1920, 16, 24
         ts = [torch.from_numpy(synth.symmetrise(synth.blur_target(h, wd, SIGMA, seed=3001 + k))).to(dev)
@@ -536,7 +546,9 @@ def run_config(args):
         nm = torch.zeros((nt, ns), dtype=torch.float32, device=dev)
         run = lambda: plan.ospr(ts, ns, 0, 3000, bits_out=bits, nmse_out=nm)  # noqa: E731
         units, unit, bpu = nt * ns, "subframes/s", 44 * h * wd
-    if args.strip_width is None:
+    if w == "dbs128":
+        pass  # no strip width: one cluster per item
+    elif args.strip_width is None:
         plan.autotune()  # GS strip widths (OSPR keeps its row-major field)
     else:
         plan.set_strip_width(0, args.strip_width)
@@ -557,9 +569,12 @@ def run_config(args):
     peak, src = measured_peaks()
     gbs = bpu * units / (ms / 1e3) / 1e9
     line = {"workload": w, "value": units / (ms / 1e3), "unit": unit, "ms_per_run": ms,
-            "alg_bytes_per_unit": bpu, "achieved_gb_s": gbs, "frac_of_hbm": gbs / peak, "peak_source": src,
+            "alg_bytes_per_unit": bpu, "achieved_gb_s": gbs if bpu else None,
+            "frac_of_hbm": gbs / peak if bpu else None, "peak_source": src,
             "final_nmse": nm.cpu().numpy()[:, -1].tolist()[:4], "steps": args.steps, "warmup": args.warmup,
-            "graph": True, ("strip_width" if args.strip_width is not None else "autotuned_strip_width"): width}
+            "graph": True}
+    if w != "dbs128":
+        line["strip_width" if args.strip_width is not None else "autotuned_strip_width"] = width
     plan.close()
     print(json.dumps(line))
 
@@ -655,10 +670,12 @@ def main():
     ap.add_argument("--cpu-iters", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="gs2048",
-                    choices=["gs2048", "batch", "gd", "gs256", "fresnel1024", "ospr", "mraf2048", "hio2048"],
+                    choices=["gs2048", "batch", "gd", "gs256", "fresnel1024", "ospr", "mraf2048", "hio2048",
+                             "dbs128"],
                     help="gs2048: the headline line; batch: the mixed-size serving batch; "
                          "gd: gradient descent vs multi-plane GS, time to NMSE; gs256 / fresnel1024 / ospr: "
-                         "the other single-GPU configurations; mraf2048 / hio2048: the MRAF and HIO variants of GS")
+                         "the other single-GPU configurations; mraf2048 / hio2048: the MRAF and HIO variants of GS; "
+                         "dbs128: direct binary search, 128^2, two sweeps")
     ap.add_argument("--strip-width", type=int, default=None,
                     help="gs256 / fresnel1024 / mraf2048 / hio2048: use this strip width (-1: the whole run in "
                          "one thread-block cluster) instead of the autotuner's choice")
@@ -671,7 +688,7 @@ def main():
     if args.workload == "gd":
         run_gd(args)
         return
-    if args.workload in ("gs256", "fresnel1024", "ospr", "mraf2048", "hio2048"):
+    if args.workload in ("gs256", "fresnel1024", "ospr", "mraf2048", "hio2048", "dbs128"):
         run_config(args)
         return
     if args.impl == "reference":

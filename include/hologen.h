@@ -180,6 +180,25 @@ HG_API hg_status hg_hio_run(hg_plan* plan, const float* const* target_amp, const
                             float* const* phase_out, uint8_t* const* level_out, float* nmse_out, void* stream);
 
 /*
+ * Direct binary search (section "Algorithm Libraries": the DS algorithm class and the single-pixel
+ * replay updater FFTUpdaterCuda; reading: Seldowitz, Allebach & Sweeney 1987) on a binary plan
+ * (quant_levels 2, one plane, no illumination profile).  From h_0 = P_2(exp(i phi_0)) (init_phase
+ * as in hg_gs_run, or the Philox draw from seed), each of n_sweeps sweeps visits the SLM pixels in
+ * row-major order and keeps the flip h_p -> -h_p when it strictly lowers the NMSE of
+ * |F(h c)|^2 against A^2 (optimal scale); the replay is updated by the single-pixel change
+ * -2 h_p c_p exp(-2 pi i (k m / H + l n / W)) (unnormalised) instead of a new transform.
+ *  phase_out / level_out  as in hg_gs_run (phase 0 or pi, level 0 or 1), after the last sweep
+ *  nmse_out               NULL or device float32 [n_items][n_sweeps + 1]: NMSE after s sweeps
+ * Each item runs in one thread-block cluster of ceil(H W / 4096) CTAs (replay plane in registers,
+ * one cluster barrier per trial flip); items of at most 65536 pixels (HG_ERR_UNSUPPORTED_SIZE
+ * beyond, or where the device cannot run the cluster).  Errors: HG_ERR_INVALID_ARG for a plan
+ * that is not binary, multi-plane or illuminated, n_sweeps outside 0..10000, and bad pointers.
+ */
+HG_API hg_status hg_dbs_run(hg_plan* plan, const float* const* target_amp, const float* const* init_phase,
+                            uint64_t seed, int32_t n_sweeps, float* const* phase_out, uint8_t* const* level_out,
+                            float* nmse_out, void* stream);
+
+/*
  * One-Step Phase-Retrieval (Cable, Buckley et al.; section "Algorithm Libraries",
  * HoloGenAlgOSPRCuda): for every item (target t) and subframe s = 0..n_subframes-1
  *   E = A exp(2 pi i u),  u = (x >> 8) 2^-24,  x = word 0 of Philox4x32-10 with counter

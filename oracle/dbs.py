@@ -24,9 +24,9 @@ from .project import slm_project
 
 def pixel_basis(h_: int, w_: int, m: int, n: int) -> np.ndarray:
     """The unitary DFT of a unit impulse at SLM pixel (m, n): exp(-2 pi i (k m / H + l n / W)) / sqrt(HW)."""
-    k = np.arange(h_)[:, None]
-    l_ = np.arange(w_)[None, :]
-    return np.exp(-2j * np.pi * (k * m / h_ + l_ * n / w_)) / np.sqrt(h_ * w_)
+    ey = np.exp(-2j * np.pi * ((np.arange(h_) * m) % h_) / h_)
+    ex = np.exp(-2j * np.pi * ((np.arange(w_) * n) % w_) / w_)
+    return np.outer(ey, ex) / np.sqrt(h_ * w_)
 
 
 def flip_update(r: np.ndarray, h: np.ndarray, m: int, n: int, c=None) -> np.ndarray:

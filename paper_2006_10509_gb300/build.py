@@ -64,6 +64,7 @@ def build(verbose: bool = False, jobs: int | None = None) -> str:
     units = [(os.path.join(CSRC, "hg_len.cu"), os.path.join(BUILD, f"hg_len_{n}.o"), [f"-DHG_LEN={n}"]) for n in lengths()]
     units.append((os.path.join(CSRC, "hg_api.cu"), os.path.join(BUILD, "hg_api.o"), []))
     units.append((os.path.join(CSRC, "hg_noalloc.cu"), os.path.join(BUILD, "hg_noalloc.o"), []))
+    units.append((os.path.join(CSRC, "hg_dbs.cu"), os.path.join(BUILD, "hg_dbs.o"), []))
     todo = [u for u in units if not os.path.exists(u[1]) or os.path.getmtime(u[1]) < newest]
     jobs = jobs or max(1, min(len(todo), os.cpu_count() or 4))
     logs = []

@@ -22,6 +22,7 @@
 #endif
 
 #include "hologen.h"
+#include "hg_dbs.h"
 #include "hg_kernels.cuh"
 #include "hg_launch.h"
 
@@ -99,12 +100,12 @@ constexpr int kMaxItems = 256;
 enum Kind {
   K_ROW_INIT = 0, K_ROW_GS, K_COL_GS, K_COL_NMSE, K_ROW_FFT, K_COL_FFT, K_ROW_OSPR, K_COL_OSPR,
   K_ROW_MP_INIT, K_ROW_MP, K_ROW_GD_FWD, K_COL_GD_FWD, K_COL_GD_BWD, K_ROW_GD_BWD, K_AMP_ENERGY, K_FINALIZE,
-  K_TILE_TARGET, K_GS_CLUSTER, K_NUM_KINDS
+  K_TILE_TARGET, K_GS_CLUSTER, K_DBS, K_NUM_KINDS
 };
 const char* const kKindNames[K_NUM_KINDS] = {"row_init",   "row_gs",     "col_gs",     "col_nmse",  "row_fft",
                                              "col_fft",    "row_ospr",   "col_ospr",   "row_mp_init", "row_mp",
                                              "row_gd_fwd", "col_gd_fwd", "col_gd_bwd", "row_gd_bwd",
-                                             "amp_energy", "finalize", "tile_target", "gs_cluster"};
+                                             "amp_energy", "finalize", "tile_target", "gs_cluster", "dbs"};
 constexpr int kMaxLevels = 256;
 
 struct SizeClass {
@@ -180,6 +181,7 @@ struct hg_plan {
   std::vector<SizeClass> classes;
   std::vector<int> item_class, item_slot;
   std::map<int, float2*> tw;
+  std::map<int, float2*> roots;  // direct binary search: exp(-2 pi i j / N), j < N, per length
   float2* lev = nullptr;
   float* lev_phase = nullptr;
   std::vector<const float*> illum;  // per item SLM illumination amplitude (nullptr: uniform)
@@ -1020,6 +1022,89 @@ hg_status run_maybe_graph(hg_plan* p, const std::vector<uintptr_t>& key,
 }
 
 // MRAF and HIO: GS with a signal region (the rest of the replay plane is the noise region).
+// Direct binary search for every size class: per chunk of items the start h_0 and its replay
+// R_0 = F(h_0 c) (the GS prologue's row pass, then forward column FFTs in place, unnormalised),
+// then one cluster launch that runs every sweep.
+hg_status dbs_enqueue(hg_plan* p, const float* const* target_amp, const float* const* init_phase, uint64_t seed,
+                      int32_t n_sweeps, float* const* phase_out, uint8_t* const* level_out, float* nmse_out,
+                      cudaStream_t st) {
+  hg_status s;
+  for (size_t ci : p->class_order) {
+    const SizeClass& c = p->classes[ci];
+    const int cl = (c.H * c.W + hg::kDbsPixelsPerCta - 1) / hg::kDbsPixelsPerCta;
+    const int chunk = std::min(hg::kMaxBatch, hg::kDbsMaxBatch);
+    for (size_t c0 = 0; c0 < c.items.size(); c0 += chunk) {
+      const int nb = (int)std::min<size_t>(chunk, c.items.size() - c0);
+      hg::PassArgs a{};
+      fill_common(p, c, 0, a);
+      a.n_items = nb;
+      a.seed = seed;
+      a.scale = 1.f;
+      hg::DbsArgs d{};
+      d.H = c.H;
+      d.W = c.W;
+      d.n_sweeps = n_sweeps;
+      d.nmse_stride = n_sweeps + 1;
+      d.seed = seed;
+      d.wy = p->roots.at(c.H);
+      d.wx = p->roots.at(c.W);
+      d.cx = a.cx;
+      d.cy = a.cy;
+      d.centred = p->centred ? 1 : 0;
+      d.nmse = nmse_out;
+      for (int k = 0; k < nb; ++k) {
+        const int item = c.items[c0 + k];
+        a.item_index[k] = item;
+        a.class_slot[k] = (int)(c0 + k);
+        a.phase_in[k] = init_phase ? init_phase[item] : nullptr;
+        a.out[k] = c.field + (c0 + k) * (size_t)c.H * c.W;
+        d.field[k] = a.out[k];
+        d.target[k] = target_amp[item];
+        d.phase_in[k] = a.phase_in[k];
+        d.phase_out[k] = phase_out ? phase_out[item] : nullptr;
+        d.level_out[k] = level_out ? level_out[item] : nullptr;
+        d.item_index[k] = item;
+      }
+      if ((s = launch(p, K_ROW_INIT, c.rk->init[0], dim3(c.row_blocks(), nb), c.rk->nt, c.rk->smem, a, st)) != HG_OK)
+        return s;
+      if ((s = launch(p, K_COL_FFT, c.ck->fft[0][0], dim3(c.col_blocks(), nb), c.ck->nt, c.ck->smem, a, st)) !=
+          HG_OK)
+        return s;
+      // the search itself: one cluster of cl CTAs per item
+      cudaEvent_t ea = nullptr, eb = nullptr;
+      if (p->timing) {
+        ea = p->get_event();
+        eb = p->get_event();
+        if (ea && eb) cudaEventRecordWithFlags(ea, st, p->capturing ? cudaEventRecordExternal : cudaEventRecordDefault);
+      }
+      cudaLaunchConfig_t cfg{};
+      cfg.gridDim = dim3(cl, nb);
+      cfg.blockDim = dim3(hg::kDbsThreads);
+      cfg.dynamicSmemBytes = (size_t)hg::dbs_smem(c.H, c.W);
+      cfg.stream = st;
+      cudaLaunchAttribute attr{};
+      attr.id = cudaLaunchAttributeClusterDimension;
+      attr.val.clusterDim.x = (unsigned)cl;
+      attr.val.clusterDim.y = 1;
+      attr.val.clusterDim.z = 1;
+      cfg.attrs = &attr;
+      cfg.numAttrs = 1;
+      void* args[] = {(void*)&d};
+      const cudaError_t e = cudaLaunchKernelExC(&cfg, hg::dbs_kernel(), args);
+      if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+      p->launches++;
+      if (ea && eb) {
+        cudaEventRecordWithFlags(eb, st, p->capturing ? cudaEventRecordExternal : cudaEventRecordDefault);
+        p->pending.push_back({ea, eb, K_DBS});
+      } else {
+        if (ea) p->event_pool.push_back(ea);
+        if (eb) p->event_pool.push_back(eb);
+      }
+    }
+  }
+  return HG_OK;
+}
+
 hg_status region_run(hg_plan* p, const char* name, const float* const* target_amp,
                      const uint8_t* const* signal_mask, float mix, bool hio, float beta,
                      const float* const* init_phase, uint64_t seed, int32_t n_iter, float* const* phase_out,
@@ -1139,6 +1224,79 @@ hg_status hg_mraf_run(hg_plan* p, const float* const* target_amp, const uint8_t*
   if (!(mix > 0.f && mix <= 1.f)) return fail(HG_ERR_INVALID_ARG, "mix must be in (0, 1]");
   return region_run(p, "MRAF", target_amp, signal_mask, mix, false, 0.f, init_phase, seed, n_iter, phase_out,
                     level_out, nmse_out, stream);
+}
+
+hg_status hg_dbs_run(hg_plan* p, const float* const* target_amp, const float* const* init_phase, uint64_t seed,
+                     int32_t n_sweeps, float* const* phase_out, uint8_t* const* level_out, float* nmse_out,
+                     void* stream) {
+  if (!p) return fail(HG_ERR_INVALID_ARG, "plan is NULL");
+  if (p->P != 1) return fail(HG_ERR_INVALID_ARG, "DBS needs a single-plane plan");
+  if (p->levels != 2) return fail(HG_ERR_INVALID_ARG, "DBS needs a binary plan (quant_levels 2)");
+  if (!p->illum.empty()) return fail(HG_ERR_INVALID_ARG, "DBS does not take an illumination profile");
+  if (n_sweeps < 0 || n_sweeps > 10000) return fail(HG_ERR_INVALID_ARG, "n_sweeps must be 0..10000");
+  if (!target_amp) return fail(HG_ERR_INVALID_ARG, "target_amp is NULL");
+  for (int i = 0; i < p->n_items; ++i)
+    if ((int64_t)p->H[i] * p->W[i] > (int64_t)hg::kDbsMaxCluster * hg::kDbsPixelsPerCta)
+      return fail(HG_ERR_UNSUPPORTED_SIZE, "item %d: DBS takes at most %d pixels", i,
+                  hg::kDbsMaxCluster * hg::kDbsPixelsPerCta);
+  DeviceGuard g(p->device);
+  if (!g.ok) return fail(HG_ERR_CUDA, "cannot select device %d", p->device);
+  hg_status s;
+  for (int i = 0; i < p->n_items; ++i) {
+    const size_t px = (size_t)p->H[i] * p->W[i];
+    if ((s = check_ptr(p, target_amp[i], px * 4, 4, "target_amp", i)) != HG_OK) return s;
+    if (init_phase && init_phase[i] && (s = check_ptr(p, init_phase[i], px * 4, 4, "init_phase", i)) != HG_OK)
+      return s;
+    if (phase_out && phase_out[i] && (s = check_ptr(p, phase_out[i], px * 4, 4, "phase_out", i)) != HG_OK) return s;
+    if (level_out && level_out[i] && (s = check_ptr(p, level_out[i], px, 1, "level_out", i)) != HG_OK) return s;
+  }
+  if (nmse_out && (s = check_ptr(p, nmse_out, (size_t)p->n_items * (n_sweeps + 1) * 4, 4, "nmse_out", 0)) != HG_OK)
+    return s;
+  hg::dbs_set_attrs();
+  for (const SizeClass& c : p->classes) {
+    for (int len : {c.H, c.W}) {
+      if (p->roots.count(len)) continue;
+      std::vector<float2> r(len);
+      const double two_pi = 6.283185307179586476925286766559;
+      for (int j = 0; j < len; ++j)
+        r[j] = make_float2((float)std::cos(two_pi * j / len), (float)-std::sin(two_pi * j / len));
+      float2* dptr = nullptr;
+      if ((s = upload(p, &dptr, r, "DBS root table")) != HG_OK) return s;
+      p->roots[len] = dptr;
+    }
+    // the class's cluster must fit on the device
+    const int cl = (c.H * c.W + hg::kDbsPixelsPerCta - 1) / hg::kDbsPixelsPerCta;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(cl, 1);
+    cfg.blockDim = dim3(hg::kDbsThreads);
+    cfg.dynamicSmemBytes = (size_t)hg::dbs_smem(c.H, c.W);
+    cudaLaunchAttribute attr{};
+    attr.id = cudaLaunchAttributeClusterDimension;
+    attr.val.clusterDim.x = (unsigned)cl;
+    attr.val.clusterDim.y = 1;
+    attr.val.clusterDim.z = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, hg::dbs_kernel(), &cfg) != cudaSuccess || n < 1) {
+      cudaGetLastError();
+      return fail(HG_ERR_UNSUPPORTED_SIZE, "%dx%d: the device cannot run a DBS cluster of %d CTAs", c.H, c.W, cl);
+    }
+  }
+  std::vector<uintptr_t> key{5, (uintptr_t)n_sweeps, (uintptr_t)seed, (uintptr_t)nmse_out};
+  if (p->graph)
+    for (int i = 0; i < p->n_items; ++i) {
+      key.push_back((uintptr_t)target_amp[i]);
+      key.push_back((uintptr_t)(init_phase ? init_phase[i] : nullptr));
+      key.push_back((uintptr_t)(phase_out ? phase_out[i] : nullptr));
+      key.push_back((uintptr_t)(level_out ? level_out[i] : nullptr));
+    }
+  return run_maybe_graph(
+      p, key,
+      [&](cudaStream_t q) {
+        return dbs_enqueue(p, target_amp, init_phase, seed, n_sweeps, phase_out, level_out, nmse_out, q);
+      },
+      (cudaStream_t)stream);
 }
 
 hg_status hg_hio_run(hg_plan* p, const float* const* target_amp, const uint8_t* const* signal_mask, float beta,

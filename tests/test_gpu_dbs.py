@@ -1,0 +1,157 @@
+"""GPU parity of direct binary search (hg_dbs_run) against the FP64 oracle (oracle.dbs).
+
+After one sweep the GPU's kept flips are known exactly (a pixel changed sign iff its flip was
+kept), so the oracle replays the sweep trial by trial, in FP64, following the GPU's decisions; at
+every trial the GPU must have taken the oracle's decision unless the two NMSE values tie to within
+1e-6 of the NMSE (where float32 replay fields may order them either way), and such ties must be
+rare.  Also: the NMSE of the start and of the result against the oracle's, the NMSE curve over
+sweeps, zero sweeps, several items and mixed sizes in one plan (each as its own one-item plan),
+the seeded start (the GS prologue's), display-order targets, argument errors.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import dbs as odbs
+from oracle import optics
+from oracle.fft import fft2
+from oracle.metrics import nmse
+from tests.helpers import check_nmse, cuda_device
+
+LAM, PITCH = 532e-9, 8e-6
+TIE = 1e-6
+
+
+def _run(hg, dev, sizes, targets, phases, n_sweeps, z=None, flags=0, seed=0):
+    import torch
+
+    kw = dict(propagation=hg.HG_FRESNEL, wavelength_m=LAM, pitch_m=PITCH, z_m=[z]) if z else {}
+    with hg.Plan([s[0] for s in sizes], [s[1] for s in sizes], quant_levels=2, flags=flags, **kw) as plan:
+        lv = [torch.zeros(s, dtype=torch.uint8, device=dev) for s in sizes]
+        ph = [torch.zeros(s, dtype=torch.float32, device=dev) for s in sizes]
+        nm = torch.zeros((len(sizes), n_sweeps + 1), dtype=torch.float32, device=dev)
+        plan.dbs([torch.from_numpy(np.ascontiguousarray(t)).to(dev) for t in targets], n_sweeps,
+                 init_phase=None if phases is None else [torch.from_numpy(p).to(dev) for p in phases], seed=seed,
+                 phase_out=ph, level_out=lv, nmse_out=nm)
+        plan.sync()
+        return [x.cpu().numpy() for x in lv], [x.cpu().numpy() for x in ph], nm.cpu().numpy()
+
+
+def _binary_phase(h, w, seed):
+    rng = np.random.default_rng(seed)
+    return (np.pi * rng.integers(0, 2, (h, w))).astype(np.float32)
+
+
+def _replay_check(a, phi0, q1, c):
+    """Replays one sweep following the GPU's decisions; returns (ties, final oracle NMSE)."""
+    t = a.astype(np.float64) ** 2
+    h0, r0 = odbs.start(phi0.astype(np.float64), c)
+    kept = (q1 == 1) != (h0 < 0)
+    ties = []
+
+    def follow(p, e_old, e_new):
+        m, n = divmod(p, a.shape[1])
+        gpu = bool(kept[m, n])
+        if gpu != (e_new < e_old):
+            assert abs(e_new - e_old) <= TIE * e_old, f"trial {p}: GPU {gpu}, oracle NMSE {e_old:.9g} -> {e_new:.9g}"
+            ties.append(p)
+        return gpu
+
+    h1, r1, _ = odbs.sweep(h0, r0, t, c, decide=follow)
+    assert np.array_equal(h1 < 0, q1 == 1)
+    return ties, nmse(np.abs(r1) ** 2, t), nmse(np.abs(r0) ** 2, t)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("h, w, z", [(32, 32, None), (64, 64, None), (64, 128, None), (128, 128, None),
+                                     (64, 64, 0.02), (120, 64, None)])
+def test_dbs_one_sweep_follows_the_oracle(h, w, z):
+    import paper_2006_10509_gb300 as hg
+
+    dev = cuda_device()
+    a = synth.blur_target(h, w, 1.5, seed=h + w)
+    phi0 = _binary_phase(h, w, 7)
+    c = optics.chirp(h, w, LAM, PITCH, z) if z else None
+    q, ph, nm = _run(hg, dev, [(h, w)], [a], [phi0], 1, z)
+    assert set(np.unique(ph[0])) <= {0.0, np.float32(np.pi)}
+    assert np.array_equal(ph[0] > 0, q[0] == 1)
+    ties, e1, e0 = _replay_check(a, phi0, q[0], c)
+    assert len(ties) <= max(2, h * w // 1000)
+    check_nmse(nm[0], [e0, e1], rtol=1e-4)
+    assert nm[0, 1] < nm[0, 0]
+
+
+@pytest.mark.gpu
+def test_dbs_nmse_curve_over_sweeps():
+    import paper_2006_10509_gb300 as hg
+
+    dev = cuda_device()
+    a = synth.spots_target(64, 64, 6, seed=11)
+    phi0 = _binary_phase(64, 64, 12)
+    q, _, nm = _run(hg, dev, [(64, 64)], [a], [phi0], 4)
+    assert np.all(np.diff(nm[0].astype(np.float64)) <= 1e-7)
+    h = np.where(q[0] == 1, -1.0, 1.0)
+    check_nmse(nm[0, -1:], [nmse(np.abs(fft2(h)) ** 2, a.astype(np.float64) ** 2)], rtol=1e-4)
+
+
+@pytest.mark.gpu
+def test_dbs_items_zero_sweeps_and_seeded_start():
+    import torch
+    import paper_2006_10509_gb300 as hg
+
+    dev = cuda_device()
+    sizes = [(32, 32), (64, 32), (128, 128), (32, 32)]
+    targets = [synth.blur_target(h, w, 1.5, seed=20 + i) for i, (h, w) in enumerate(sizes)]
+    phases = [_binary_phase(h, w, 30 + i) for i, (h, w) in enumerate(sizes)]
+    q, _, nm = _run(hg, dev, sizes, targets, phases, 2)
+    for i in range(len(sizes)):
+        q1, _, nm1 = _run(hg, dev, [sizes[i]], [targets[i]], [phases[i]], 2)
+        assert np.array_equal(q[i], q1[0]), i
+        assert np.array_equal(nm[i], nm1[0]), i
+    # zero sweeps: the projected start and its NMSE
+    q0, _, nm0 = _run(hg, dev, sizes[:1], targets[:1], phases[:1], 0)
+    assert np.array_equal(q0[0], (phases[0] > 1.0).astype(np.uint8))
+    h0 = np.where(phases[0] > 1.0, -1.0, 1.0)
+    check_nmse(nm0[0], [nmse(np.abs(fft2(h0)) ** 2, targets[0].astype(np.float64) ** 2)], rtol=1e-4)
+    # seeded start: the binary start of the GS path (same Philox draw and projection)
+    qs, _, _ = _run(hg, dev, sizes[:1], targets[:1], None, 0, seed=99)
+    with hg.Plan([32], [32], quant_levels=2) as plan:
+        lv = torch.zeros((32, 32), dtype=torch.uint8, device=dev)
+        plan.gs([torch.from_numpy(targets[0]).to(dev)], 0, seed=99, level_out=[lv])
+        plan.sync()
+    assert np.array_equal(qs[0], lv.cpu().numpy())
+
+
+@pytest.mark.gpu
+def test_dbs_centred_targets():
+    import paper_2006_10509_gb300 as hg
+
+    dev = cuda_device()
+    a = synth.spots_target(64, 128, 5, seed=40)
+    phi0 = _binary_phase(64, 128, 41)
+    q, _, nm = _run(hg, dev, [(64, 128)], [a], [phi0], 1)
+    qc, _, nmc = _run(hg, dev, [(64, 128)], [np.fft.fftshift(a)], [phi0], 1, flags=hg.HG_TARGET_CENTRED)
+    assert np.array_equal(q[0], qc[0])
+    assert np.array_equal(nm, nmc)
+
+
+@pytest.mark.gpu
+def test_dbs_argument_errors():
+    import torch
+    import paper_2006_10509_gb300 as hg
+
+    dev = cuda_device()
+    a = torch.ones((64, 64), dtype=torch.float32, device=dev)
+    with hg.Plan([64], [64], quant_levels=4) as plan:
+        with pytest.raises(hg.HologenError) as e:
+            plan.dbs([a], 1)
+        assert e.value.status == hg.HG_ERR_INVALID_ARG
+    with hg.Plan([64], [64], quant_levels=2) as plan:
+        with pytest.raises(hg.HologenError) as e:
+            plan.dbs([a], -1)
+        assert e.value.status == hg.HG_ERR_INVALID_ARG
+    big = torch.ones((512, 256), dtype=torch.float32, device=dev)
+    with hg.Plan([512], [256], quant_levels=2) as plan:
+        with pytest.raises(hg.HologenError) as e:
+            plan.dbs([big], 1)
+        assert e.value.status == hg.HG_ERR_UNSUPPORTED_SIZE
