@@ -1,4 +1,5 @@
-"""Direct binary search (DBS) with a single-pixel replay update (FP64).  Test infrastructure only.
+"""Direct binary search (DBS) with a single-pixel replay update, and simulated annealing over the same
+trial flips (FP64).  Test infrastructure only.
 
 The paper lists a direct-search algorithm for binary holograms and a replay updater that changes a
 single pixel (section "Algorithm Libraries": the DS algorithm class and FFTUpdaterCuda) without
@@ -75,3 +76,38 @@ def dbs(target_amp, init_phase, n_sweeps: int, c=None):
         curve.append(nmse(np.abs(r) ** 2, t))
     q = (h < 0).astype(np.int64)
     return {"h": h, "phase": np.pi * q.astype(np.float64), "q": q, "nmse": np.array(curve)}
+
+
+def sa(target_amp, init_phase, n_sweeps: int, t0: float, alpha: float, seed: int, item: int = 0, c=None):
+    """Simulated annealing over the same trial flips (FP64).
+
+    The paper lists a simulated-annealing class beside direct search (section "Algorithm
+    Libraries") without formulas.  Reading taken here (Kirkpatrick, Gelatt & Vecchi 1983, with the
+    flips, order and energy of DBS): sweep s runs at temperature T_s = t0 alpha^s (T_0 = t0, then
+    multiplied by alpha after each sweep); a trial flip is kept when it lowers the NMSE E, or
+    otherwise when u < exp(-(E' - E) / T_s), with u the Philox draw of (pixel, sweep)
+    (philox.anneal_uniform).  Returns dict(h, phase, q, nmse[n_sweeps+1])."""
+    from .philox import anneal_uniform
+
+    a = np.asarray(target_amp, dtype=np.float64)
+    t = a * a
+    h, r = start(init_phase, c)
+    curve = [nmse(np.abs(r) ** 2, t)]
+    temp = float(t0)
+    for s in range(n_sweeps):
+        u = anneal_uniform(h.size, s, item, seed)
+        h, r, _ = sweep(h, r, t, c, decide=metropolis(u, temp))
+        curve.append(nmse(np.abs(r) ** 2, t))
+        temp *= alpha
+    q = (h < 0).astype(np.int64)
+    return {"h": h, "phase": np.pi * q.astype(np.float64), "q": q, "nmse": np.array(curve)}
+
+
+def metropolis(u: np.ndarray, temp: float):
+    """The acceptance rule of one annealing sweep: keep an improving flip, otherwise keep it when
+    u[p] < exp(-(E' - E) / T)."""
+
+    def rule(p, e_old, e_new):
+        return e_new < e_old or u[p] < np.exp(-(e_new - e_old) / temp)
+
+    return rule

@@ -63,3 +63,14 @@ def init_uniform(n_pixels: int, item: int, seed: int) -> np.ndarray:
     k1 = ((seed >> 32) ^ int(item)) & 0xFFFFFFFF
     x0, _, _, _ = philox4x32_10((p, 0, 1, 0), (k0, k1))
     return (x0 >> np.uint32(8)).astype(np.float64) * (2.0 ** -24)
+
+
+def anneal_uniform(n_pixels: int, sweep: int, item: int, seed: int) -> np.ndarray:
+    """Acceptance draws of simulated annealing for the trial flips p = 0..n-1 of one sweep: word 0 of
+    Philox4x32-10 with counter (p, sweep, 2, 0) and key (seed_lo, seed_hi ^ item), u = (x >> 8) 2^-24."""
+    p = np.arange(n_pixels, dtype=np.uint64)
+    seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+    k0 = seed & 0xFFFFFFFF
+    k1 = ((seed >> 32) ^ int(item)) & 0xFFFFFFFF
+    x0, _, _, _ = philox4x32_10((p, sweep, 2, 0), (k0, k1))
+    return (x0 >> np.uint32(8)).astype(np.float64) * (2.0 ** -24)

@@ -101,3 +101,52 @@ def test_reachable_target_is_a_fixed_point_and_zero_sweeps_return_the_start():
     out0 = dbs.dbs(synth.blur_target(h_, w_, 1.0, seed=7), phi0, 0)
     assert np.array_equal(out0["h"], hstar) and out0["nmse"].shape == (1,)
     assert np.array_equal(out0["q"], (hstar < 0).astype(np.int64))
+
+
+# ------------------------------------------------------------------ simulated annealing
+
+
+def test_annealing_at_vanishing_temperature_is_dbs():
+    h_, w_ = 8, 8
+    a = synth.blur_target(h_, w_, 1.0, seed=8).astype(np.float64)
+    phi0 = synth.uniform_phase(h_, w_, seed=9).astype(np.float64)
+    ref = dbs.dbs(a, phi0, 3)
+    out = dbs.sa(a, phi0, 3, 1e-300, 0.5, seed=10)
+    assert np.array_equal(out["h"], ref["h"])
+    assert np.allclose(out["nmse"], ref["nmse"], rtol=0, atol=0)
+
+
+def test_annealing_at_huge_temperature_keeps_every_flip():
+    h_, w_ = 6, 10
+    a = synth.blur_target(h_, w_, 1.0, seed=11).astype(np.float64)
+    phi0 = synth.uniform_phase(h_, w_, seed=12).astype(np.float64)
+    h0, _ = dbs.start(phi0)
+    out = dbs.sa(a, phi0, 1, 1e300, 1.0, seed=13)
+    assert np.array_equal(out["h"], -h0)
+    out2 = dbs.sa(a, phi0, 2, 1e300, 1.0, seed=13)
+    assert np.array_equal(out2["h"], h0)
+
+
+def test_annealing_rule_uses_the_pixel_and_sweep_draws():
+    """The kept worsening flips of one sweep are exactly those whose draw u[p] lies below
+    exp(-(E' - E) / T), recomputed here from full transforms."""
+    h_, w_ = 6, 6
+    a = synth.blur_target(h_, w_, 1.0, seed=14).astype(np.float64)
+    t = a * a
+    phi0 = synth.uniform_phase(h_, w_, seed=15).astype(np.float64)
+    temp = 2e-3
+    out = dbs.sa(a, phi0, 1, temp, 0.9, seed=16, item=3)
+    from oracle.philox import anneal_uniform
+
+    u = anneal_uniform(h_ * w_, 0, 3, 16)
+    h, _ = dbs.start(phi0)
+    for p in range(h_ * w_):
+        m, n = divmod(p, w_)
+        e_old = nmse(np.abs(fft2(h)) ** 2, t)
+        hf = h.copy()
+        hf[m, n] = -hf[m, n]
+        e_new = nmse(np.abs(fft2(hf)) ** 2, t)
+        if e_new < e_old or u[p] < np.exp(-(e_new - e_old) / temp):
+            h = hf
+    assert np.array_equal(h, out["h"])
+    assert 0 < np.sum(out["h"] != dbs.start(phi0)[0]) < h_ * w_
