@@ -199,6 +199,17 @@ HG_API hg_status hg_dbs_run(hg_plan* plan, const float* const* target_amp, const
                             float* nmse_out, void* stream);
 
 /*
+ * Simulated annealing (section "Algorithm Libraries": the SA algorithm class; reading: Kirkpatrick,
+ * Gelatt & Vecchi 1983) over the trial flips of hg_dbs_run, with its arguments, outputs, limits
+ * and errors: sweep s runs at temperature T_s = t0 alpha^s (t0 > 0 finite, alpha in (0, 1]); a flip
+ * that does not lower the NMSE E is still kept when u < exp(-(E' - E) / T_s), with u = (x >> 8) 2^-24
+ * and x word 0 of Philox4x32-10 with counter (pixel, s, 2, 0) and key (seed_lo, seed_hi ^ item).
+ */
+HG_API hg_status hg_sa_run(hg_plan* plan, const float* const* target_amp, const float* const* init_phase,
+                           uint64_t seed, int32_t n_sweeps, double t0, double alpha, float* const* phase_out,
+                           uint8_t* const* level_out, float* nmse_out, void* stream);
+
+/*
  * One-Step Phase-Retrieval (Cable, Buckley et al.; section "Algorithm Libraries",
  * HoloGenAlgOSPRCuda): for every item (target t) and subframe s = 0..n_subframes-1
  *   E = A exp(2 pi i u),  u = (x >> 8) 2^-24,  x = word 0 of Philox4x32-10 with counter

@@ -25,7 +25,7 @@ __all__ = [
     "hg_plan_launch_count", "hg_gs_run_noalloc", "hg_ospr_run", "hg_gd_step", "hg_gd_forward",
     "hg_gd_backward", "hologram_loss", "hg_plan_set_graph", "hg_plan_item_latency", "hg_plan_autotune",
     "hg_plan_strip_width", "hg_plan_set_strip_width", "HG_PLAN_AUTOTUNE", "hg_mraf_run",
-    "hg_plan_set_illumination", "hg_hio_run", "HG_TARGET_CENTRED", "HG_STRIP_CLUSTER", "hg_dbs_run",
+    "hg_plan_set_illumination", "hg_hio_run", "HG_TARGET_CENTRED", "HG_STRIP_CLUSTER", "hg_dbs_run", "hg_sa_run",
 ]
 
 HG_OK, HG_ERR_INVALID_ARG, HG_ERR_UNSUPPORTED_SIZE, HG_ERR_OUT_OF_MEMORY = 0, 1, 2, 3
@@ -93,6 +93,8 @@ _SIGNATURES = {
     "hg_hio_run": (ctypes.c_int, [_VP, _PP, _PP, ctypes.c_float, _PP, ctypes.c_uint64, ctypes.c_int32, _PP, _PP,
                                   _VP, _VP]),
     "hg_dbs_run": (ctypes.c_int, [_VP, _PP, _PP, ctypes.c_uint64, ctypes.c_int32, _PP, _PP, _VP, _VP]),
+    "hg_sa_run": (ctypes.c_int, [_VP, _PP, _PP, ctypes.c_uint64, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
+                                 _PP, _PP, _VP, _VP]),
     "hg_plan_item_latency": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double)]),
     "hg_plan_autotune": (ctypes.c_int, [_VP, _VP]),
     "hg_plan_strip_width": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
@@ -227,6 +229,14 @@ def hg_dbs_run(plan: int, target_amp, init_phase=None, seed: int = 0, n_sweeps: 
     _check(load().hg_dbs_run(plan, _ptr_array(target_amp), _ptr_array(init_phase), seed, n_sweeps,
                              _ptr_array(phase_out), _ptr_array(level_out),
                              None if nmse_out is None else _data_ptr(nmse_out), _stream(stream)), "hg_dbs_run")
+
+
+def hg_sa_run(plan: int, target_amp, t0: float, alpha: float, init_phase=None, seed: int = 0, n_sweeps: int = 1,
+              phase_out=None, level_out=None, nmse_out=None, stream=None):
+    """Simulated annealing for every item of a binary single-plane plan (see hologen.h)."""
+    _check(load().hg_sa_run(plan, _ptr_array(target_amp), _ptr_array(init_phase), seed, n_sweeps, t0, alpha,
+                            _ptr_array(phase_out), _ptr_array(level_out),
+                            None if nmse_out is None else _data_ptr(nmse_out), _stream(stream)), "hg_sa_run")
 
 
 def hg_hio_run(plan: int, target_amp, beta: float, signal_mask=None, init_phase=None, seed: int = 0,
@@ -399,6 +409,11 @@ class Plan:
     def dbs(self, target_amp, n_sweeps, init_phase=None, seed=0, phase_out=None, level_out=None, nmse_out=None,
             stream=None):
         hg_dbs_run(self.handle, target_amp, init_phase, seed, n_sweeps, phase_out, level_out, nmse_out, stream)
+
+    def sa(self, target_amp, n_sweeps, t0, alpha, init_phase=None, seed=0, phase_out=None, level_out=None,
+           nmse_out=None, stream=None):
+        hg_sa_run(self.handle, target_amp, t0, alpha, init_phase, seed, n_sweeps, phase_out, level_out, nmse_out,
+                  stream)
 
     def hio(self, target_amp, beta, n_iter, signal_mask=None, init_phase=None, seed=0, phase_out=None, level_out=None,
             nmse_out=None, stream=None):

@@ -1026,8 +1026,8 @@ hg_status run_maybe_graph(hg_plan* p, const std::vector<uintptr_t>& key,
 // R_0 = F(h_0 c) (the GS prologue's row pass, then forward column FFTs in place, unnormalised),
 // then one cluster launch that runs every sweep.
 hg_status dbs_enqueue(hg_plan* p, const float* const* target_amp, const float* const* init_phase, uint64_t seed,
-                      int32_t n_sweeps, float* const* phase_out, uint8_t* const* level_out, float* nmse_out,
-                      cudaStream_t st) {
+                      int32_t n_sweeps, bool anneal, double t0, double alpha, float* const* phase_out,
+                      uint8_t* const* level_out, float* nmse_out, cudaStream_t st) {
   hg_status s;
   for (size_t ci : p->class_order) {
     const SizeClass& c = p->classes[ci];
@@ -1051,6 +1051,9 @@ hg_status dbs_enqueue(hg_plan* p, const float* const* target_amp, const float* c
       d.cx = a.cx;
       d.cy = a.cy;
       d.centred = p->centred ? 1 : 0;
+      d.anneal = anneal ? 1 : 0;
+      d.t0 = t0;
+      d.alpha = alpha;
       d.nmse = nmse_out;
       for (int k = 0; k < nb; ++k) {
         const int item = c.items[c0 + k];
@@ -1158,6 +1161,10 @@ hg_status region_run(hg_plan* p, const char* name, const float* const* target_am
   return run_maybe_graph(p, key, [&](cudaStream_t q) { return gs_enqueue(p, call, q); }, (cudaStream_t)stream);
 }
 
+hg_status search_run(hg_plan* p, const char* name, const float* const* target_amp, const float* const* init_phase,
+                     uint64_t seed, int32_t n_sweeps, bool anneal, double t0, double alpha,
+                     float* const* phase_out, uint8_t* const* level_out, float* nmse_out, void* stream);
+
 }  // namespace
 
 extern "C" {
@@ -1229,15 +1236,36 @@ hg_status hg_mraf_run(hg_plan* p, const float* const* target_amp, const uint8_t*
 hg_status hg_dbs_run(hg_plan* p, const float* const* target_amp, const float* const* init_phase, uint64_t seed,
                      int32_t n_sweeps, float* const* phase_out, uint8_t* const* level_out, float* nmse_out,
                      void* stream) {
+  return search_run(p, "DBS", target_amp, init_phase, seed, n_sweeps, false, 0.0, 1.0, phase_out, level_out,
+                    nmse_out, stream);
+}
+
+hg_status hg_sa_run(hg_plan* p, const float* const* target_amp, const float* const* init_phase, uint64_t seed,
+                    int32_t n_sweeps, double t0, double alpha, float* const* phase_out, uint8_t* const* level_out,
+                    float* nmse_out, void* stream) {
+  if (!(t0 > 0.0) || !std::isfinite(t0)) return fail(HG_ERR_INVALID_ARG, "t0 must be finite and > 0");
+  if (!(alpha > 0.0 && alpha <= 1.0)) return fail(HG_ERR_INVALID_ARG, "alpha must be in (0, 1]");
+  return search_run(p, "SA", target_amp, init_phase, seed, n_sweeps, true, t0, alpha, phase_out, level_out,
+                    nmse_out, stream);
+}
+
+}  // extern "C"
+
+namespace {
+
+// Direct binary search and simulated annealing: checks, tables, then the search launches.
+hg_status search_run(hg_plan* p, const char* name, const float* const* target_amp, const float* const* init_phase,
+                     uint64_t seed, int32_t n_sweeps, bool anneal, double t0, double alpha,
+                     float* const* phase_out, uint8_t* const* level_out, float* nmse_out, void* stream) {
   if (!p) return fail(HG_ERR_INVALID_ARG, "plan is NULL");
-  if (p->P != 1) return fail(HG_ERR_INVALID_ARG, "DBS needs a single-plane plan");
-  if (p->levels != 2) return fail(HG_ERR_INVALID_ARG, "DBS needs a binary plan (quant_levels 2)");
-  if (!p->illum.empty()) return fail(HG_ERR_INVALID_ARG, "DBS does not take an illumination profile");
+  if (p->P != 1) return fail(HG_ERR_INVALID_ARG, "%s needs a single-plane plan", name);
+  if (p->levels != 2) return fail(HG_ERR_INVALID_ARG, "%s needs a binary plan (quant_levels 2)", name);
+  if (!p->illum.empty()) return fail(HG_ERR_INVALID_ARG, "%s does not take an illumination profile", name);
   if (n_sweeps < 0 || n_sweeps > 10000) return fail(HG_ERR_INVALID_ARG, "n_sweeps must be 0..10000");
   if (!target_amp) return fail(HG_ERR_INVALID_ARG, "target_amp is NULL");
   for (int i = 0; i < p->n_items; ++i)
     if ((int64_t)p->H[i] * p->W[i] > (int64_t)hg::kDbsMaxCluster * hg::kDbsPixelsPerCta)
-      return fail(HG_ERR_UNSUPPORTED_SIZE, "item %d: DBS takes at most %d pixels", i,
+      return fail(HG_ERR_UNSUPPORTED_SIZE, "item %d: %s takes at most %d pixels", i, name,
                   hg::kDbsMaxCluster * hg::kDbsPixelsPerCta);
   DeviceGuard g(p->device);
   if (!g.ok) return fail(HG_ERR_CUDA, "cannot select device %d", p->device);
@@ -1283,7 +1311,11 @@ hg_status hg_dbs_run(hg_plan* p, const float* const* target_amp, const float* co
       return fail(HG_ERR_UNSUPPORTED_SIZE, "%dx%d: the device cannot run a DBS cluster of %d CTAs", c.H, c.W, cl);
     }
   }
-  std::vector<uintptr_t> key{5, (uintptr_t)n_sweeps, (uintptr_t)seed, (uintptr_t)nmse_out};
+  uint64_t tb[2];
+  std::memcpy(&tb[0], &t0, sizeof t0);
+  std::memcpy(&tb[1], &alpha, sizeof alpha);
+  std::vector<uintptr_t> key{(uintptr_t)(anneal ? 6 : 5), (uintptr_t)n_sweeps, (uintptr_t)seed, (uintptr_t)nmse_out,
+                             (uintptr_t)tb[0], (uintptr_t)tb[1]};
   if (p->graph)
     for (int i = 0; i < p->n_items; ++i) {
       key.push_back((uintptr_t)target_amp[i]);
@@ -1294,10 +1326,15 @@ hg_status hg_dbs_run(hg_plan* p, const float* const* target_amp, const float* co
   return run_maybe_graph(
       p, key,
       [&](cudaStream_t q) {
-        return dbs_enqueue(p, target_amp, init_phase, seed, n_sweeps, phase_out, level_out, nmse_out, q);
+        return dbs_enqueue(p, target_amp, init_phase, seed, n_sweeps, anneal, t0, alpha, phase_out, level_out,
+                           nmse_out, q);
       },
       (cudaStream_t)stream);
 }
+
+}  // namespace
+
+extern "C" {
 
 hg_status hg_hio_run(hg_plan* p, const float* const* target_amp, const uint8_t* const* signal_mask, float beta,
                      const float* const* init_phase, uint64_t seed, int32_t n_iter, float* const* phase_out,

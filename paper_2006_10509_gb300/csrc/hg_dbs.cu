@@ -1,5 +1,7 @@
 // Direct binary search on the GPU (section "Algorithm Libraries": the DS class and the single-pixel
-// replay updater FFTUpdaterCuda; reading: Seldowitz, Allebach & Sweeney 1987).
+// replay updater FFTUpdaterCuda; reading: Seldowitz, Allebach & Sweeney 1987), and simulated
+// annealing over the same trial flips (the SA class of the same section; reading: Kirkpatrick,
+// Gelatt & Vecchi 1983).
 //
 // A binary hologram h in {+1, -1} is improved one SLM pixel at a time, in row-major order: the trial
 // flip of pixel p = (m, n) changes the unnormalised replay R = F(h c) by
@@ -144,6 +146,8 @@ __global__ void __launch_bounds__(kDbsThreads, 1) k_dbs(const __grid_constant__ 
   for (int j = 0; j < kDbsValues; ++j) nvalid += (rank * kDbsPixelsPerCta + t + j * kDbsThreads) < px;
 
   double s_it = 0.0, s_ii = 0.0, s_tt = 0.0;  // thread 0: the cluster's sums
+  double temp = d.t0;                         // thread 0: annealing temperature of the sweep
+  const uint2 key = make_uint2((uint32_t)d.seed, (uint32_t)(d.seed >> 32) ^ (uint32_t)d.item_index[k]);
   int par = 0;
   for (int sweep = 0;; ++sweep) {
     // exact sums at the sweep boundary (NMSE of the current hologram)
@@ -172,6 +176,7 @@ __global__ void __launch_bounds__(kDbsThreads, 1) k_dbs(const __grid_constant__ 
       par ^= 1;
     }
     if (sweep == d.n_sweeps) break;
+    if (sweep > 0) temp *= d.alpha;
 #pragma unroll
     for (int j = 0; j < kDbsValues; ++j) iy[j] = ix[j] = 0;
     for (int m = 0; m < H; ++m) {
@@ -201,7 +206,14 @@ __global__ void __launch_bounds__(kDbsThreads, 1) k_dbs(const __grid_constant__ 
           double tot[3];
           gather_sums(slots, par, cl, tot);
           const double nit = s_it + tot[0], nii = s_ii + tot[1];
-          const bool keep = nii > 0.0 && s_ii > 0.0 && nit * nit * s_ii > s_it * s_it * nii;
+          bool keep = nii > 0.0 && s_ii > 0.0 && nit * nit * s_ii > s_it * s_it * nii;
+          if (!keep && d.anneal && nii > 0.0 && s_ii > 0.0 && s_tt > 0.0) {
+            // Metropolis: E' - E = (S_IT^2 / S_II - S_IT'^2 / S_II') / S_TT >= 0
+            const double de = (s_it * s_it / s_ii - nit * nit / nii) / s_tt;
+            const uint4 x = philox4x32_10(make_uint4((uint32_t)p, (uint32_t)sweep, 2u, 0u), key);
+            const double u = (double)(x.x >> 8) * (1.0 / 16777216.0);
+            keep = u < exp(-de / temp);
+          }
           if (keep) {
             s_it = nit;
             s_ii = nii;

@@ -24,6 +24,11 @@ struct DbsArgs {
   const float2* cx;         // Fresnel chirp along a row (W), nullptr for Fourier
   const float2* cy;         // Fresnel chirp along a column (H)
   int centred;              // targets in display order (DC at (H/2, W/2))
+  // simulated annealing (anneal = 1): a flip that does not lower the NMSE E is still kept when
+  // u < exp(-(E' - E) / T_s), T_s = t0 alpha^s, u from Philox4x32-10 word 0 with counter
+  // (pixel, sweep, 2, 0) and key (seed_lo, seed_hi ^ item), u = (x >> 8) 2^-24
+  int anneal;
+  double t0, alpha;
   float* nmse;              // [item][n_sweeps + 1] or nullptr
   const float2* field[kDbsMaxBatch];  // R_0 = unnormalised F(h_0 c), row-major [H][W] (plan workspace)
   const float* target[kDbsMaxBatch];  // amplitude A [H][W]

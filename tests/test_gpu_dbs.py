@@ -1,4 +1,5 @@
-"""GPU parity of direct binary search (hg_dbs_run) against the FP64 oracle (oracle.dbs).
+"""GPU parity of direct binary search (hg_dbs_run) and simulated annealing (hg_sa_run) against the
+FP64 oracle (oracle.dbs).
 
 After one sweep the GPU's kept flips are known exactly (a pixel changed sign iff its flip was
 kept), so the oracle replays the sweep trial by trial, in FP64, following the GPU's decisions; at
@@ -155,3 +156,82 @@ def test_dbs_argument_errors():
         with pytest.raises(hg.HologenError) as e:
             plan.dbs([big], 1)
         assert e.value.status == hg.HG_ERR_UNSUPPORTED_SIZE
+
+
+# ------------------------------------------------------------------ simulated annealing
+
+
+def _run_sa(hg, dev, sizes, targets, phases, n_sweeps, t0, alpha, seed, z=None):
+    import torch
+
+    kw = dict(propagation=hg.HG_FRESNEL, wavelength_m=LAM, pitch_m=PITCH, z_m=[z]) if z else {}
+    with hg.Plan([s[0] for s in sizes], [s[1] for s in sizes], quant_levels=2, **kw) as plan:
+        lv = [torch.zeros(s, dtype=torch.uint8, device=dev) for s in sizes]
+        nm = torch.zeros((len(sizes), n_sweeps + 1), dtype=torch.float32, device=dev)
+        plan.sa([torch.from_numpy(t).to(dev) for t in targets], n_sweeps, t0, alpha,
+                init_phase=[torch.from_numpy(p).to(dev) for p in phases], seed=seed, level_out=lv, nmse_out=nm)
+        plan.sync()
+        return [x.cpu().numpy() for x in lv], nm.cpu().numpy()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("h, w, z, t0", [(32, 32, None, 1e-3), (64, 64, 0.02, 3e-4), (64, 128, None, 3e-4)])
+def test_sa_one_sweep_follows_the_oracle(h, w, z, t0):
+    """As for DBS, with the Metropolis rule: where the GPU and the oracle decide differently, the
+    oracle's NMSE change must tie with 0 or with the acceptance threshold -T ln u to 1e-6 of the NMSE."""
+    import paper_2006_10509_gb300 as hg
+    from oracle.philox import anneal_uniform
+
+    dev = cuda_device()
+    a = synth.blur_target(h, w, 1.5, seed=h + 2 * w)
+    phi0 = _binary_phase(h, w, 8)
+    c = optics.chirp(h, w, LAM, PITCH, z) if z else None
+    seed = 21
+    q, nm = _run_sa(hg, dev, [(h, w)], [a], [phi0], 1, t0, 0.8, seed, z)
+    t = a.astype(np.float64) ** 2
+    h0, r0 = odbs.start(phi0.astype(np.float64), c)
+    kept = (q[0] == 1) != (h0 < 0)
+    u = anneal_uniform(h * w, 0, 0, seed)
+    rule = odbs.metropolis(u, t0)
+    ties, worse_kept = [], 0
+
+    def follow(p, e_old, e_new):
+        nonlocal worse_kept
+        m, n = divmod(p, w)
+        gpu = bool(kept[m, n])
+        if gpu != rule(p, e_old, e_new):
+            de = e_new - e_old
+            assert min(abs(de), abs(de + t0 * np.log(u[p]))) <= TIE * e_old, f"trial {p}"
+            ties.append(p)
+        worse_kept += gpu and e_new >= e_old
+        return gpu
+
+    h1, r1, _ = odbs.sweep(h0, r0, t, c, decide=follow)
+    assert len(ties) <= max(2, h * w // 1000)
+    assert worse_kept > 0
+    check_nmse(nm[0], [nmse(np.abs(r0) ** 2, t), nmse(np.abs(r1) ** 2, t)], rtol=1e-4)
+
+
+@pytest.mark.gpu
+def test_sa_temperature_limits_and_errors():
+    import torch
+    import paper_2006_10509_gb300 as hg
+
+    dev = cuda_device()
+    a = synth.blur_target(64, 64, 1.5, seed=50)
+    phi0 = _binary_phase(64, 64, 51)
+    q_dbs, _, nm_dbs = _run(hg, dev, [(64, 64)], [a], [phi0], 2)
+    q_cold, nm_cold = _run_sa(hg, dev, [(64, 64)], [a], [phi0], 2, 1e-300, 0.5, 3)
+    assert np.array_equal(q_cold[0], q_dbs[0])
+    assert np.array_equal(nm_cold, nm_dbs)
+    q0 = (phi0 > 1.0).astype(np.uint8)
+    q_hot, _ = _run_sa(hg, dev, [(64, 64)], [a], [phi0], 1, 1e300, 1.0, 3)
+    assert np.array_equal(q_hot[0], 1 - q0)
+    q_hot2, _ = _run_sa(hg, dev, [(64, 64)], [a], [phi0], 2, 1e300, 1.0, 3)
+    assert np.array_equal(q_hot2[0], q0)
+    ta = torch.from_numpy(a).to(dev)
+    with hg.Plan([64], [64], quant_levels=2) as plan:
+        for t0, alpha in ((0.0, 0.5), (-1.0, 0.5), (1e-3, 0.0), (1e-3, 1.5), (float("inf"), 0.5)):
+            with pytest.raises(hg.HologenError) as e:
+                plan.sa([ta], 1, t0, alpha)
+            assert e.value.status == hg.HG_ERR_INVALID_ARG
