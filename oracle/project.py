@@ -10,6 +10,15 @@ SLM constraint (phase-only SLM, unit modulus):
   q = floor(a N / (2 pi) + 1/2) mod N, h = exp(i phi_q).  An exact midpoint between two levels goes
   to the higher index (mod N).  N = 2 is binary {0, pi}: h = +1 / -1.  g == 0 gives q = 0.
 
+Multi-amplitude / complex-modulation SLM (section "Application": the SLM type option offers a
+multi-amplitude SLM, MultiAmpSLM, with its own settings; reading): the pixel takes one of M given
+complex values m_q (e.g. the measured responses of its drive levels); the projection is the
+nearest of them in the complex plane, h = m_q with q = argmin |g - m_q| (the lowest index on a
+tie).  For M unit-modulus values
+at equal angles this is the N-level rule above.  Unlike the phase-only sets this one is not a
+cone, so the scale of g matters: g is taken in the unitary scale of the loop (the replay target
+carries the energy of a unit-modulus SLM field).
+
 Replay constraint (amplitude replacement): R' = A * R / |R|, with R / |R| = 1 where R == 0.
 """
 from __future__ import annotations
@@ -45,9 +54,28 @@ def level_field(q: np.ndarray, n_levels: int) -> np.ndarray:
     return h
 
 
-def slm_project(g: np.ndarray, n_levels: int):
-    """SLM projection.  Returns (h, q): q is None for continuous phase (n_levels == 0)."""
+def table_project(g: np.ndarray, table) -> tuple:
+    """Nearest entry of a finite set of complex SLM values (Euclidean distance; on a tie the lowest
+    index).  Returns (h, q) with q the entry index (int64)."""
     g = np.asarray(g, dtype=np.complex128)
+    t = np.asarray(table, dtype=np.complex128).ravel()
+    q = np.zeros(g.shape, dtype=np.int64)
+    best = np.abs(g - t[0]) ** 2
+    for i in range(1, t.size):
+        d = np.abs(g - t[i]) ** 2
+        closer = d < best
+        q = np.where(closer, i, q)
+        best = np.where(closer, d, best)
+    return t[q], q
+
+
+def slm_project(g: np.ndarray, n_levels):
+    """SLM projection.  Returns (h, q): q is None for continuous phase (n_levels == 0).  n_levels may
+    also be an array of complex SLM values (a multi-amplitude / complex-modulation SLM), projected
+    onto by table_project."""
+    g = np.asarray(g, dtype=np.complex128)
+    if isinstance(n_levels, np.ndarray):
+        return table_project(g, n_levels)
     if n_levels == 0:
         mag = np.abs(g)
         h = np.where(mag > 0.0, g / np.where(mag > 0.0, mag, 1.0), 1.0 + 0.0j)
