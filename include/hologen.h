@@ -150,6 +150,20 @@ HG_API hg_status hg_gs_run(hg_plan* plan, const float* const* target_amp, const 
 HG_API hg_status hg_plan_set_illumination(hg_plan* plan, const float* const* illum_amp);
 
 /*
+ * Multi-amplitude / complex-modulation SLM (section "Application": the SLM type option offers a
+ * multi-amplitude SLM, MultiAmpSLM).  levels: host array of 2 n_levels floats, the (re, im) pairs
+ * of the n_levels (2..256) complex values a pixel can take; copied.  hg_gs_run, hg_mraf_run and
+ * hg_hio_run then project the SLM-plane field g onto the nearest of them, h = m_q with
+ * q = argmin |g - m_q| (float32 squared distance, the lowest index on a tie), with g in the
+ * unitary scale of the loop (the replay target at the energy of a unit-modulus field);
+ * level_out[i] receives q and phase_out[i] arg(m_q) in [0, 2 pi).  NULL or n_levels 0 restores the
+ * plan's phase-only levels.  Drops captured graphs.  Errors: HG_ERR_INVALID_ARG for a multi-plane
+ * or illuminated plan, n_levels outside 2..256 or a non-finite value; direct binary search,
+ * annealing and gradient descent reject a plan with a table.
+ */
+HG_API hg_status hg_plan_set_slm_levels(hg_plan* plan, const float* levels, int32_t n_levels);
+
+/*
  * Mixed-region amplitude freedom (MRAF; Pasienski & DeMarco 2008): the reading taken here of the
  * paper's "other iterative Fourier transform approaches" (section "Algorithm Libraries",
  * HoloGenAlgGSCuda).  Same loop, arguments and outputs as hg_gs_run on a single-plane plan, except

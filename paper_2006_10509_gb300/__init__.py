@@ -25,7 +25,7 @@ __all__ = [
     "hg_plan_launch_count", "hg_gs_run_noalloc", "hg_ospr_run", "hg_gd_step", "hg_gd_forward",
     "hg_gd_backward", "hologram_loss", "hg_plan_set_graph", "hg_plan_item_latency", "hg_plan_autotune",
     "hg_plan_strip_width", "hg_plan_set_strip_width", "HG_PLAN_AUTOTUNE", "hg_mraf_run",
-    "hg_plan_set_illumination", "hg_hio_run", "HG_TARGET_CENTRED", "HG_STRIP_CLUSTER", "hg_dbs_run", "hg_sa_run",
+    "hg_plan_set_illumination", "hg_hio_run", "HG_TARGET_CENTRED", "HG_STRIP_CLUSTER", "hg_dbs_run", "hg_sa_run", "hg_plan_set_slm_levels",
 ]
 
 HG_OK, HG_ERR_INVALID_ARG, HG_ERR_UNSUPPORTED_SIZE, HG_ERR_OUT_OF_MEMORY = 0, 1, 2, 3
@@ -88,6 +88,7 @@ _SIGNATURES = {
     "hg_plan_launch_count": (ctypes.c_int64, [_VP]),
     "hg_plan_set_graph": (ctypes.c_int, [_VP, ctypes.c_int32]),
     "hg_plan_set_illumination": (ctypes.c_int, [_VP, _PP]),
+    "hg_plan_set_slm_levels": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float), ctypes.c_int32]),
     "hg_mraf_run": (ctypes.c_int, [_VP, _PP, _PP, ctypes.c_float, _PP, ctypes.c_uint64, ctypes.c_int32, _PP, _PP,
                                    _VP, _VP]),
     "hg_hio_run": (ctypes.c_int, [_VP, _PP, _PP, ctypes.c_float, _PP, ctypes.c_uint64, ctypes.c_int32, _PP, _PP,
@@ -213,6 +214,17 @@ def hg_gs_run(plan: int, target_amp, init_phase=None, seed: int = 0, n_iter: int
 def hg_plan_set_illumination(plan: int, illum_amp=None):
     """Per-item SLM illumination amplitude tensors (None entries: uniform); None clears."""
     _check(load().hg_plan_set_illumination(plan, _ptr_array(illum_amp)), "hg_plan_set_illumination")
+
+
+def hg_plan_set_slm_levels(plan: int, levels=None):
+    """Complex SLM values (a sequence of complex numbers) for a multi-amplitude SLM; None restores the
+    plan's phase-only levels."""
+    if levels is None:
+        _check(load().hg_plan_set_slm_levels(plan, None, 0), "hg_plan_set_slm_levels")
+        return
+    vals = [complex(v) for v in levels]
+    arr = (ctypes.c_float * (2 * len(vals)))(*[x for v in vals for x in (v.real, v.imag)])
+    _check(load().hg_plan_set_slm_levels(plan, arr, len(vals)), "hg_plan_set_slm_levels")
 
 
 def hg_mraf_run(plan: int, target_amp, mix: float, signal_mask=None, init_phase=None, seed: int = 0,
@@ -456,6 +468,9 @@ class Plan:
 
     def item_latency_ms(self) -> list[float]:
         return hg_plan_item_latency(self.handle, len(self.heights))
+
+    def set_slm_levels(self, levels=None):
+        hg_plan_set_slm_levels(self.handle, levels)
 
     def set_illumination(self, illum_amp=None):
         self._illum = illum_amp  # the plan reads these buffers on every run: keep them alive

@@ -184,6 +184,11 @@ struct hg_plan {
   std::map<int, float2*> roots;  // direct binary search: exp(-2 pi i j / N), j < N, per length
   float2* lev = nullptr;
   float* lev_phase = nullptr;
+  // the plan's phase-only level set (quant_levels and its tables), kept while a multi-amplitude
+  // table is set (levels = -M, lev / lev_phase pointing at the table)
+  int levels0 = 0;
+  float2* lev0 = nullptr;
+  float* lev_phase0 = nullptr;
   std::vector<const float*> illum;  // per item SLM illumination amplitude (nullptr: uniform)
   std::vector<void*> allocs;
   // run order, graphs and latency stamps
@@ -715,6 +720,9 @@ hg_status hg_plan_create(const hg_plan_desc* d, hg_plan** out) {
     }
     if ((s = upload(p, &p->lev, lev, "level table")) != HG_OK) return bail(s);
     if ((s = upload(p, &p->lev_phase, ph, "level table")) != HG_OK) return bail(s);
+    p->levels0 = p->levels;
+    p->lev0 = p->lev;
+    p->lev_phase0 = p->lev_phase;
   }
   if ((s = p->alloc(&p->stamps, 1 + p->classes.size(), "latency stamps")) != HG_OK) return bail(s);
   if (cudaMemset(p->stamps, 0, (1 + p->classes.size()) * sizeof(unsigned long long)) != cudaSuccess)
@@ -846,7 +854,7 @@ hg_status gs_class(hg_plan* p, const SizeClass& c, const GsCall& g, cudaStream_t
     a.beta = g.beta;
     bool lit = false;
     for (int k = 0; k < nb; ++k) lit = lit || a.illum[k] != nullptr;
-    if (c.tile == -1 && P == 1 && g.mix == 0.f && !lit) {
+    if (c.tile == -1 && P == 1 && g.mix == 0.f && !lit && p->levels >= 0) {
       // the whole run in one launch: one cluster per item, the field in the cluster's shared memory
       for (int k = 0; k < nb; ++k) {
         const int item = c.items[c0 + k];
@@ -906,14 +914,16 @@ hg_status gs_class(hg_plan* p, const SizeClass& c, const GsCall& g, cudaStream_t
         return s;
       continue;
     }
-    if (g.mix > 0.f) {
-      // MRAF / HIO: the signal region's target energy, for the absolute scale of m A_s
+    if (g.mix > 0.f || p->levels < 0) {
+      // MRAF / HIO: the signal region's target energy, for the absolute scale of m A_s; a
+      // multi-amplitude SLM: the target energy, for the unitary scale of the field it projects
       const dim3 genergy(strips, nb), gfin(1, nb);
       if ((s = launch(p, K_AMP_ENERGY, (const void*)&k_amp_energy, genergy, 256, 0, a, st)) != HG_OK) return s;
       if ((s = launch(p, K_FINALIZE, (const void*)&hg::k_finalize<2>, gfin, 32, 0, a, st)) != HG_OK) return s;
     }
-    // extended kernels only when the run uses MRAF or an illumination profile
-    const int x = (g.mix > 0.f || lit) ? 1 : 0;
+    // extended kernels only when the run uses MRAF / HIO, an illumination profile or a
+    // multi-amplitude SLM
+    const int x = (g.mix > 0.f || lit || p->levels < 0) ? 1 : 0;
     const void* k_init = tiled ? c.rk->init_t[ti][x] : c.rk->init[x];
     const void* k_row[2] = {tiled ? c.rk->gs_t[ti][0][x] : c.rk->gs[0][x],
                             tiled ? c.rk->gs_t[ti][1][x] : c.rk->gs[1][x]};
@@ -1214,6 +1224,7 @@ hg_status hg_plan_set_illumination(hg_plan* p, const float* const* illum_amp) {
     return HG_OK;
   }
   if (p->P != 1) return fail(HG_ERR_INVALID_ARG, "an illumination profile needs a single-plane plan");
+  if (p->levels < 0) return fail(HG_ERR_INVALID_ARG, "an illumination profile needs a phase-only SLM");
   DeviceGuard g(p->device);
   if (!g.ok) return fail(HG_ERR_CUDA, "cannot select device %d", p->device);
   hg_status s;
@@ -1222,6 +1233,46 @@ hg_status hg_plan_set_illumination(hg_plan* p, const float* const* illum_amp) {
         (s = check_ptr(p, illum_amp[i], (size_t)p->H[i] * p->W[i] * 4, 4, "illum_amp", i)) != HG_OK)
       return s;
   p->illum.assign(illum_amp, illum_amp + p->n_items);
+  return HG_OK;
+}
+
+hg_status hg_plan_set_slm_levels(hg_plan* p, const float* levels, int32_t n_levels) {
+  if (!p) return fail(HG_ERR_INVALID_ARG, "plan is NULL");
+  if (!levels || n_levels == 0) {
+    p->levels = p->levels0;
+    p->lev = p->lev0;
+    p->lev_phase = p->lev_phase0;
+    for (auto& slot : p->gslot) p->drop_graph(slot);
+    return HG_OK;
+  }
+  if (p->P != 1) return fail(HG_ERR_INVALID_ARG, "a multi-amplitude SLM needs a single-plane plan");
+  if (!p->illum.empty()) return fail(HG_ERR_INVALID_ARG, "a multi-amplitude SLM does not take an illumination profile");
+  if (n_levels < 2 || n_levels > kMaxLevels)
+    return fail(HG_ERR_INVALID_ARG, "n_levels must be 2..%d", kMaxLevels);
+  std::vector<float2> lev(n_levels);
+  std::vector<float> ph(n_levels);
+  const double two_pi = 6.283185307179586476925286766559;
+  for (int q = 0; q < n_levels; ++q) {
+    const float re = levels[2 * q], im = levels[2 * q + 1];
+    if (!std::isfinite(re) || !std::isfinite(im)) return fail(HG_ERR_INVALID_ARG, "level %d is not finite", q);
+    lev[q] = make_float2(re, im);
+    double a = std::atan2((double)im, (double)re);
+    if (a < 0.0) a += two_pi;
+    if (a >= two_pi) a = 0.0;
+    ph[q] = (float)a;
+  }
+  DeviceGuard g(p->device);
+  if (!g.ok) return fail(HG_ERR_CUDA, "cannot select device %d", p->device);
+  HG_CUDA(cudaDeviceSynchronize(), "device error");
+  float2* dl = nullptr;
+  float* dp = nullptr;
+  hg_status s;
+  if ((s = upload(p, &dl, lev, "SLM level table")) != HG_OK) return s;
+  if ((s = upload(p, &dp, ph, "SLM level table")) != HG_OK) return s;
+  p->levels = -n_levels;
+  p->lev = dl;
+  p->lev_phase = dp;
+  for (auto& slot : p->gslot) p->drop_graph(slot);
   return HG_OK;
 }
 

@@ -171,7 +171,8 @@ __device__ __forceinline__ void pdl_wait_then_release() {
 struct PassArgs {
   int n_items;
   int H, W;
-  int n_levels;            // 0 continuous, 2 binary, N >= 3 N-level
+  int n_levels;            // 0 continuous, 2 binary, N >= 3 N-level; -M: M complex SLM values in lev
+                           // (multi-amplitude SLM; extended GS kernels only)
   int iter;                // iteration / subframe index of the pass
   int col_blocks;          // column-pass blocks per (item, plane): partial triples to add
   int finalize;            // row passes: 1 = first add up the preceding column pass's NMSE
@@ -280,6 +281,32 @@ __device__ __forceinline__ float2 slm_project(float2 g, int n_levels, const floa
   if (qq >= n_levels) qq -= n_levels;
   q = qq;
   return __ldg(&lev[qq]);
+}
+
+// Multi-amplitude / complex-modulation SLM: the nearest of the m complex values lev[0..m) (squared
+// distance in float32; the lowest index on a tie).
+__device__ __forceinline__ float2 table_project(float2 g, int m, const float2* __restrict__ lev, int& q) {
+  int best = 0;
+  float2 l = __ldg(&lev[0]);
+  float bd = fmaf(g.x - l.x, g.x - l.x, (g.y - l.y) * (g.y - l.y));
+  for (int i = 1; i < m; ++i) {
+    l = __ldg(&lev[i]);
+    const float dd = fmaf(g.x - l.x, g.x - l.x, (g.y - l.y) * (g.y - l.y));
+    if (dd < bd) {
+      bd = dd;
+      best = i;
+    }
+  }
+  q = best;
+  return __ldg(&lev[best]);
+}
+
+// SLM projection of the GS row kernels: the extended instances also take a table of -n_levels
+// complex values (n_levels < 0); the plain ones keep the phase-only sets.
+template <bool EXT>
+__device__ __forceinline__ float2 slm_project_x(float2 g, int n_levels, const float2* __restrict__ lev, int& q) {
+  if (EXT && n_levels < 0) return table_project(g, -n_levels, lev, q);
+  return slm_project(g, n_levels, lev, q);
 }
 
 __device__ __forceinline__ float phase_0_2pi(float2 h) {
@@ -495,7 +522,7 @@ __global__ void __launch_bounds__(RowCfg<W, TW>::NT, RowCfg<W, TW>::MINB) k_row_
         e = init_unit((uint32_t)p, a.seed, a.item_index[k]);
       }
       int q;
-      h = slm_project(e, a.n_levels, a.lev, q);
+      h = slm_project_x<EXT>(e, a.n_levels, a.lev, q);
       if (po) po[p] = a.n_levels ? __ldg(&a.lev_phase[q]) : phase_0_2pi(h);
       if (lo) lo[p] = (uint8_t)q;
       if (EXT && a.illum[k]) h = c_scale(h, __ldg(&a.illum[k][p]));  // the SLM only sets the phase
@@ -525,6 +552,13 @@ __global__ void __launch_bounds__(RowCfg<W, TW>::NT, RowCfg<W, TW>::MINB) k_row_
   FftRun<G, true, 1, typename K::Inv>::run(v, sm, t, a.tw_row);
   float* po = OUT ? a.phase_out[k] : nullptr;
   uint8_t* lo = OUT ? a.level_out[k] : nullptr;
+  // a multi-amplitude SLM's projection depends on the scale of g: bring the unnormalised field to
+  // the unitary scale of the loop (replay target at a unit-modulus field's energy): 1 / sqrt(sum A^2)
+  // for GS, 1 / (H W) under MRAF / HIO, whose column pass already scales the replacement
+  const float gscale = (EXT && a.n_levels < 0)
+                           ? (a.mix > 0.f ? 1.f / ((float)H * (float)W)
+                                          : (float)__ldcg(&a.stats[(size_t)a.class_slot[k] * 4 + 3]))
+                           : 1.f;
   for_each_slot<G, K::RM>(t, [&](int s, int b, int n) {
     const int row = row0 + b;
     float2 g = v[s];
@@ -533,8 +567,9 @@ __global__ void __launch_bounds__(RowCfg<W, TW>::NT, RowCfg<W, TW>::MINB) k_row_
       c = c_mul(__ldg(&a.cx[n]), __ldg(&a.cy[row]));
       g = c_mulc(g, c);
     }
+    if (EXT && a.n_levels < 0) g = c_scale(g, gscale);
     int q;
-    float2 h = slm_project(g, a.n_levels, a.lev, q);
+    float2 h = slm_project_x<EXT>(g, a.n_levels, a.lev, q);
     if (OUT && row < H) {
       const size_t p = (size_t)row * W + n;
       if (po) po[p] = a.n_levels ? __ldg(&a.lev_phase[q]) : phase_0_2pi(h);
