@@ -14,6 +14,16 @@
  *   hg_ospr_run                        One-Step Phase-Retrieval (HoloGenAlgOSPRCuda)
  *   hg_gd_step                         one Adam step of gradient-descent hologram optimisation
  *                                      (no counterpart in the paper)
+ *   hg_mraf_run / hg_hio_run           GS variants with a signal window: mixed-region amplitude
+ *                                      freedom and hybrid input-output ("other iterative Fourier
+ *                                      transform approaches" of HoloGenAlgGSCuda)
+ *   hg_dbs_run / hg_sa_run             direct binary search and simulated annealing with the
+ *                                      single-pixel replay update (the DS and SA classes,
+ *                                      FFTUpdaterCuda)
+ *   hg_plan_set_illumination,          SLM illumination profile; multi-amplitude / complex-
+ *   hg_plan_set_slm_levels             modulation SLM values (the MultiAmpSLM option)
+ *   hg_plan_autotune, graph mode,      strip widths, CUDA-graph replay, per-kernel timing and
+ *   timing, hg_gs_run_noalloc          a no-allocation GS call
  *
  * Conventions (every entry point):
  *  - Data pointers are DEVICE pointers owned by the caller (CUDA global memory on the plan's device).
