@@ -75,6 +75,15 @@ def test_null_plan_calls(hg):
     assert lib.hg_gs_run(None, None, None, 0, 1, None, None, None, None) == 1
     assert lib.hg_ospr_run(None, None, 1, 0, 0, None, None, None) == 1
     assert "NULL" in hg.hg_last_error()
+    assert lib.hg_mraf_run(None, None, None, 0.5, None, 0, 1, None, None, None, None) == 1
+    assert lib.hg_hio_run(None, None, None, 0.7, None, 0, 1, None, None, None, None) == 1
+    assert lib.hg_dbs_run(None, None, None, 0, 1, None, None, None, None) == 1
+    assert lib.hg_sa_run(None, None, None, 0, 1, 1e-3, 0.9, None, None, None, None) == 1
+    assert lib.hg_plan_set_slm_levels(None, None, 0) == 1
+    assert lib.hg_plan_set_illumination(None, None) == 1
+    assert lib.hg_plan_set_strip_width(None, 0, 2) == 1
+    assert lib.hg_plan_autotune(None, None) == 1
+    assert "NULL" in hg.hg_last_error()
     assert lib.hg_gs_run_noalloc(4096, 4096, 0, None, None, 0, 1, None, None, None, None) == 2
     assert "1048576" in hg.hg_last_error()
 
