@@ -337,7 +337,7 @@ HG_API int64_t hg_plan_launch_count(const hg_plan* plan);
 HG_API hg_status hg_plan_set_graph(hg_plan* plan, int32_t enabled);
 
 /*
- * Autotuner (SURVEY's plan-owned "autotune choice"; no counterpart in the paper).  Single-plane GS
+ * Autotuner (a tuning choice the plan owns; no counterpart in the paper).  Single-plane GS
  * keeps its field tiled in column strips so that a column pass reads its strip as one contiguous
  * block; the strip width trades the column pass's CTA size against the row pass's access pattern.
  * The plan starts from a measured default per column length.  hg_plan_autotune times, for every
