@@ -17,7 +17,8 @@ struct RowKernels {
   int rows;      // rows per CTA
   int nt;        // threads per CTA
   int smem;      // dynamic shared memory bytes
-  // [EXT]: the plain kernel, or the one that also applies an SLM illumination profile
+  // [EXT]: the plain kernel, or the one that also applies an SLM illumination profile or projects
+  // onto a multi-amplitude SLM table
   const void* init[2];      // k_row_init (row-major field)
   const void* gs[2][2];     // k_row_gs<OUT = false / true> (row-major field)
   // the same on a field tiled in column strips of width 2 / 4 / 8 / 16 (nullptr where the row
@@ -44,7 +45,7 @@ struct ColKernels {
   int nt;
   int smem;
   int smem_gs;              // dynamic shared memory of k_col_gs / k_col_ospr (exchange + target strip)
-  // [EXT]: the plain kernel, or the one that also takes MRAF's mixed regions
+  // [EXT]: the plain kernel, or the one that also takes the signal / noise regions of MRAF and HIO
   const void* gs[2][2];     // k_col_gs<REPLACE = false / true> (row-major field)
   // k_col_gs on the GS field tiled in strips of width 2 / 4 / 8 / 16 (gs nullptr where that
   // configuration does not exist for this length); tile: the default width (tiled_cols)
