@@ -160,6 +160,92 @@ def test_ospr_nmse_falls_with_subframes():
     assert c[15] < c[3] < c[0]
 
 
+def _binarise_by_hand(g):
+    """Nearest of {+1, -1}: -1 where Re g < 0, and on Re g == 0 where Im g > 0 (the tie rule)."""
+    q = ((g.real < 0.0) | ((g.real == 0.0) & (g.imag > 0.0))).astype(np.int64)
+    return 1.0 - 2.0 * q, q
+
+
+def _ospr_subframe_by_hand(a, subframe, target, seed, c=None):
+    """One classic OSPR subframe written out with the explicit quadruple DFT sum: theta = 2 pi u
+    (u from the Philox generator pinned by its known-answer vectors), A_s = A sqrt(HW / sum A^2),
+    g = conj(c) F^-1(A_s e^{i theta}), h = binary(g), I = |F(h c)|^2."""
+    hh, ww = a.shape
+    u = philox.ospr_uniform(hh * ww, subframe, target, seed).reshape(hh, ww)
+    a_s = a * np.sqrt(hh * ww / np.sum(a * a))
+    g = dft.dft2_bruteforce(a_s * np.exp(2j * np.pi * u), inverse=True)
+    if c is not None:
+        g = np.conj(c) * g
+    h, q = _binarise_by_hand(g)
+    r = dft.dft2_bruteforce(h if c is None else h * c)
+    return h, q, g, np.abs(r) ** 2
+
+
+@pytest.mark.parametrize("fresnel", [False, True])
+def test_ospr_subframe_by_explicit_dft(fresnel):
+    # unsymmetrised, non-square target: a forward transform in place of F^-1, theta = pi u, or A^2 in
+    # place of A change the bits here (a symmetrised target would hide the transform direction)
+    hh, ww = 6, 10
+    a = np.random.default_rng(401).uniform(0.1, 1.0, (hh, ww))
+    c = optics.chirp(hh, ww, LAM, PITCH, 0.01) if fresnel else None
+    for s, t, seed in ((0, 0, 77), (3, 2, 2**40 + 5)):
+        h, q, g, inten = _ospr_subframe_by_hand(a, s, t, seed, c)
+        sf = ospr.ospr_subframe(a, s, t, seed, 0, c)
+        assert np.array_equal(sf["q"], q)
+        np.testing.assert_array_equal(sf["h"], h)
+        np.testing.assert_allclose(sf["g"], g, rtol=0, atol=1e-12 * np.abs(g).max())
+        np.testing.assert_allclose(sf["intensity"], inten, rtol=0, atol=1e-12 * inten.max())
+    # the pin has power: each of these misreadings flips some bits on this input
+    u = philox.ospr_uniform(hh * ww, 0, 0, 77).reshape(hh, ww)
+    a_s = a * np.sqrt(hh * ww / np.sum(a * a))
+    _, q_ok, _, _ = _ospr_subframe_by_hand(a, 0, 0, 77, c)
+    wrong = [dft.dft2_bruteforce(a_s * np.exp(2j * np.pi * u)),               # forward transform
+             dft.dft2_bruteforce(a_s * np.exp(1j * np.pi * u), inverse=True),  # theta = pi u
+             dft.dft2_bruteforce(a_s ** 2 * np.exp(2j * np.pi * u), inverse=True)]  # A^2 for A
+    for gw in wrong:
+        gw = gw if c is None else np.conj(c) * gw
+        assert not np.array_equal(_binarise_by_hand(gw)[1], q_ok)
+
+
+@pytest.mark.parametrize("fresnel", [False, True])
+def test_ospr_refinement_is_binary_gs_chain(fresnel):
+    # n_iter > 0: the subframe's start followed by n_iter binary GS iterations against A
+    hh, ww = 8, 12
+    a = np.random.default_rng(402).uniform(0.1, 1.0, (hh, ww))
+    c = optics.chirp(hh, ww, LAM, PITCH, 0.01) if fresnel else None
+    h0, _, _, _ = _ospr_subframe_by_hand(a, 1, 4, 99, c)
+    for n_iter in (1, 3):
+        h = h0
+        for _ in range(n_iter):
+            st = gs.gs_step(h, a, 2, c)
+            h, q = st["h"], st["q"]
+        sf = ospr.ospr_subframe(a, 1, 4, 99, n_iter, c)
+        np.testing.assert_array_equal(sf["h"], h)
+        assert np.array_equal(sf["q"], q)
+        r = dft.dft2_bruteforce(h if c is None else h * c)
+        np.testing.assert_allclose(sf["intensity"], np.abs(r) ** 2, rtol=0,
+                                   atol=1e-12 * sf["intensity"].max())
+
+
+def test_ospr_accumulated_nmse_by_hand():
+    # nmse[s] is the optimal-scale NMSE of the mean replay intensity of subframes 0..s against A^2,
+    # here from brute-force intensities and the closed form 1 - (sum I T)^2 / (sum I^2 sum T^2)
+    hh, ww = 6, 8
+    a = np.random.default_rng(403).uniform(0.1, 1.0, (hh, ww))
+    out = ospr.ospr(a, 4, 7, 31)
+    t = a * a
+    acc = np.zeros_like(t)
+    for s in range(4):
+        _, q, _, inten = _ospr_subframe_by_hand(a, s, 7, 31)
+        assert np.array_equal(out["q"][s], q)
+        assert np.array_equal(ospr.unpack_bits(out["bits"][s], ww), q)
+        acc += inten
+        i = acc / (s + 1)
+        want = 1.0 - np.sum(i * t) ** 2 / (np.sum(i * i) * np.sum(t * t))
+        assert abs(out["nmse"][s] - want) <= 1e-12
+    np.testing.assert_allclose(out["i_acc"], acc, rtol=0, atol=1e-12 * acc.max())
+
+
 def test_ospr_bits_match_levels():
     a = synth.symmetrise(synth.blur_target(16, 40, 2.0, seed=81)).astype(np.float64)
     out = ospr.ospr(a, 3, 1, 5, n_iter=2)
