@@ -7,16 +7,24 @@ timed region starts; L2 is flushed (a 512 MiB write) before every timed step, ou
 events.  value = GS iterations/s over all ranks (weak scaling: every rank runs its own hologram).
 
 Also reported:
-  roofline      the dominant kernel's algorithmic bytes per launch / its mean launch time (CUDA
-                events recorded by the library around every launch of the last tenth of the timed
-                steps), against
-                the measured HBM copy bandwidth; traffic = DRAM bytes per launch from the committed
-                ncu summary when it was taken on the current kernel sources (else null)
+  roofline      the dominant kernel's algorithmic bytes per launch / its mean launch time, against
+                the measured HBM copy bandwidth.  The launch time is the kernel's share of device
+                time (CUDA events the library records around every launch, in extra replays of a
+                timed copy of the graph after the timed region) times the untimed step time, over
+                its launches per step; the raw event-node time is reported beside it.
+                iteration_frac: 36 B/px per GS iteration x px x it/s over the same peak.  traffic =
+                DRAM bytes per launch from the committed ncu summary when it was taken on the
+                current kernel sources (else null)
   e2e           the same metric through the public API with host buffers: every step copies the
                 target and starting phase from pinned host memory and reads back the NMSE curve and
                 the output phase inside the timed region
   cpu_baseline  the FP64 oracle (single thread) on a bounded sample of the same workload
   clocks        nvidia-smi SM clocks / throttle reasons sampled during the timed steps
+  secondary     the rest of the metric, each timed over graph replays after warm-up and given
+                with its fraction of the HBM peak: the 4-level variant of the headline, GS at
+                4096^2 (the size whose working set leaves L2), OSPR 1080x1920 (16 targets x 24
+                subframes), and gradient descent vs multi-plane GS at 2048^2 with 3 Fresnel planes
+                (time to NMSE)
 
 --impl reference times the oracle (the only reference this method has) on the same workload.
 """
@@ -198,6 +206,28 @@ print(json.dumps({{"seconds": dt, "iterations": {n}}}))
 """
 
 
+def host_cpu() -> dict:
+    """The host's logical CPU count and CPU model (lscpu, else /proc/cpuinfo, else platform)."""
+    import platform
+
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if model is None and os.path.exists("/proc/cpuinfo"):
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    return {"nproc": os.cpu_count(), "cpu_model": model or platform.processor() or platform.machine()}
+
+
 def oracle_gs_rate(n_iter: int) -> tuple[float, float]:
     """Runs n_iter FP64 oracle GS iterations (forward transform, amplitude replacement, inverse
     transform, projection) in a single-threaded subprocess; returns (iterations/s, seconds)."""
@@ -234,10 +264,12 @@ def run_reference(args):
         "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "sample": "1 GS iteration per step (the oracle's 100-iteration run "
-                                                   "takes minutes; the per-iteration NMSE is not taken)", "parallelism": "none"},
+                                                   "takes minutes; the per-iteration NMSE is not taken): the "
+                                                   "per-iteration rate is comparable with the GPU arm's, whose "
+                                                   "step is a 100-iteration run", "parallelism": "none"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": f"{args.steps} single GS iterations of the 2048x2048 workload, float64, "
-                                   "one thread"},
+                                   "one thread", **host_cpu()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -282,20 +314,14 @@ def run_ours(args):
     plan.set_timing(False)
     torch.cuda.synchronize()
 
-    # timed region: K steps, L2 flushed before each (outside the step's events)
+    # timed region: K steps of the untimed graph, L2 flushed before each (outside the step's events)
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    # per-launch kernel events (for the roofline) on the last tenth of the timed steps only (the
-    # timed graph, whose event nodes slow a step down); the totals take its latest replay
-    n_kt = max(1, args.steps // 10)
-    plan.reset_timing()
     launches0 = plan.launch_count()
     with ClockSampler(local) as clocks:
         barrier(ws)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for i, (e0, e1) in enumerate(evs):
-            if i == args.steps - n_kt:
-                plan.set_timing(True)
+        for e0, e1 in evs:
             flush.zero_()
             e0.record(stream)
             plan.gs([a], N_ITER, init_phase=[p], nmse_out=nm)
@@ -303,25 +329,50 @@ def run_ours(args):
         torch.cuda.synchronize()
         barrier(ws)
         wall = time.perf_counter() - t0
-    plan.set_timing(False)
     launches = plan.launch_count() - launches0
     dev_ms = sum(e0.elapsed_time(e1) for e0, e1 in evs)
     dev_ms = max_over_ranks(dev_ms, ws, dev)
     ms_per_step = dev_ms / args.steps
     value = ws * N_ITER * args.steps / (dev_ms / 1e3)
-    ktimes = plan.kernel_times()
     final_nmse = float(nm[0, -1].item())
+
+    # per-kernel shares of device time: extra replays (after the timed region) of the graph copy
+    # whose event nodes bracket every kernel; the totals take its latest replay.  The event nodes
+    # slow a replay down, so they give shares; a kernel's launch time is its share of the untimed
+    # step time over its launches per step.
+    plan.reset_timing()
+    plan.set_timing(True)
+    timed_ms = []
+    for _ in range(3):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plan.gs([a], N_ITER, init_phase=[p], nmse_out=nm)
+        e1.record(stream)
+        e1.synchronize()
+        timed_ms.append(e0.elapsed_time(e1))
+    plan.set_timing(False)
+    ktimes = plan.kernel_times()
+    ktot = sum(v[0] for v in ktimes.values())
+    share = {k: v[0] / ktot for k, v in ktimes.items()}
 
     # dominant kernel roofline
     dom = max(ktimes, key=lambda k: ktimes[k][0])
     dom_ms, dom_n = ktimes[dom]
+    launch_us = share[dom] * ms_per_step / dom_n * 1e3
     alg_bytes = BYTES_PER_PX.get(dom, 16) * H * W
-    achieved = alg_bytes / (dom_ms / dom_n / 1e3) / 1e9
+    achieved = alg_bytes / (launch_us / 1e6) / 1e9
     peak, peak_src = measured_peaks()
+    it_gbs = 36 * H * W * value / ws / 1e9  # one rank's GS iterations: 36 B/px each
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": peak_src, "traffic": profiled_traffic(dom),
-                "alg_bytes_per_launch": alg_bytes, "mean_launch_us": dom_ms / dom_n * 1e3,
-                "kernel_share": {k: v[0] / sum(x[0] for x in ktimes.values()) for k, v in ktimes.items()}}
+                "alg_bytes_per_launch": alg_bytes, "mean_launch_us": launch_us,
+                "launch_time": "share of device time in the timed graph copy x untimed ms_per_step / launches per step",
+                "event_node_launch_us": dom_ms / dom_n * 1e3,
+                "timed_copy_ms_per_step": statistics.median(timed_ms),
+                "iteration_bytes_per_px": 36, "iteration_achieved": it_gbs, "iteration_frac": it_gbs / peak,
+                "kernel_share": share,
+                "kernel_launch_us": {k: share[k] * ms_per_step / v[1] * 1e3 for k, v in ktimes.items()}}
 
     # end to end through the public API with host buffers
     ph_out = torch.empty((H, W), dtype=torch.float32, device=dev)
@@ -356,13 +407,23 @@ def run_ours(args):
 
     if rank != 0:
         return
+    # the rest of the metric (one GPU; rank 0 only under torchrun)
+    secondary = None
+    if not args.no_secondary:
+        secondary = {}
+        for w in ("gs2048q4", "gs4096", "ospr"):
+            secondary[w] = time_workload(w, dev, 3, 10, tune=False)
+        g = gd_vs_gs(dev, 3)
+        secondary["gd_vs_gs"] = {k: g[k] for k in ("workload", "metric", "time_to", "gd", "gs")}
+        torch.cuda.synchronize()
     cpu = None
     if ws == 1 and not args.no_cpu_baseline:
         n = args.cpu_iters
         rate, secs = oracle_gs_rate(n)
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"{n} GS iterations of the same 2048x2048 workload, "
-                         f"{secs:.1f} s, float64, one thread, NMSE not taken"}
+                         f"{secs:.1f} s, float64, one thread, NMSE not taken",
+               **host_cpu()}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -371,10 +432,11 @@ def run_ours(args):
                    "target": f"smoothed noise sigma {SIGMA} px, seed 0+rank", "init_phase": "uniform, seed 1+rank",
                    "l2": "flushed (512 MiB write) before every timed step", "parallelism": f"replicas x{ws}",
                    "launch": "CUDA graph replay per step (library graph mode)",
-                   "kernel_times": "per-kernel events of the latest timed step (graph event nodes)",
+                   "kernel_times": "shares from event nodes of a timed graph copy replayed after the timed "
+                                   "region, times the untimed step time",
                    "final_nmse": final_nmse},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-        "clocks": clocks.summary(), "wall_s": wall,
+        "clocks": clocks.summary(), "wall_s": wall, "secondary": secondary,
     }
     print(json.dumps(line))
 
@@ -464,9 +526,12 @@ def run_batch(args):
     print(json.dumps(line))
 
 
-def run_config(args):
-    """The remaining single-GPU configurations, each timed over graph replays after warm-up (GS
-    strip widths autotuned first):
+CONFIG_WORKLOADS = ("gs256", "fresnel1024", "ospr", "mraf2048", "hio2048", "dbs128", "gs2048q4", "gs4096")
+
+
+def config_workload(w: str, dev):
+    """One of the single-GPU configurations: returns (plan, run, units, unit, bytes per unit, nmse
+    buffer, tunable).  Inputs are built on the host from the seeded generators and copied once.
     gs256:       Fourier GS 256^2, continuous, 20 iterations, smoothed-noise target (seed 1001), start
                  phase seed 1002 (latency-bound: the whole field is 512 KB).
     fresnel1024: Fresnel GS 1024^2 (532 nm, 8 um, z = 0.1 m), 8-level, 100 iterations, 50-spot target
@@ -474,27 +539,32 @@ def run_config(args):
     ospr:        OSPR 1920x1080 (W x H), 16 point-symmetric smoothed-noise targets (seeds 3001..3016),
                  24 binary subframes each, Philox seed 3000, the whole batch as one graph launch.
     mraf2048:    MRAF 2048^2, continuous, signal window rows and columns [1/8, 3/8) of the FFT-order
-                 plane, m = 0.5, 100 iterations, 50-spot target (seed 6001), start phase seed 6002."""
-    import numpy as np
+                 plane, m = 0.5, 100 iterations, 50-spot target (seed 6001), start phase seed 6002.
+    hio2048:     HIO on the same problem, beta = 0.7.
+    dbs128:      direct binary search 128^2, two sweeps (seeds 7001 / 7002).
+    gs2048q4:    the headline workload (2048^2, seeds 0 / 1, 100 iterations) with 4-level phase.
+    gs4096:      Fourier GS 4096^2, continuous, 100 iterations, smoothed-noise target (seed 8001),
+                 start phase seed 8002: the field (128 MB) and target leave the L2."""
     import torch
 
     import paper_2006_10509_gb300 as hg
     import synth
-    from __graft_entry__ import build
 
-    build()
-    dev = torch.device("cuda", 0)
-    w = args.workload
-    if w == "gs256":
-        h = wd = 256
-        n_iter = 20
-        a = torch.from_numpy(synth.blur_target(h, wd, SIGMA, seed=1001)).to(dev)
-        p0 = torch.from_numpy(synth.uniform_phase(h, wd, seed=1002)).to(dev)
-        plan = hg.Plan([h], [wd])
+    def gs_plain(n, n_iter, seed_t, seed_p, levels):
+        a = torch.from_numpy(synth.blur_target(n, n, SIGMA, seed=seed_t)).to(dev)
+        p0 = torch.from_numpy(synth.uniform_phase(n, n, seed=seed_p)).to(dev)
+        plan = hg.Plan([n], [n], quant_levels=levels)
         nm = torch.zeros((1, n_iter + 1), dtype=torch.float32, device=dev)
         run = lambda: plan.gs([a], n_iter, init_phase=[p0], nmse_out=nm)  # noqa: E731
-        units, unit, bpu = n_iter, "it/s", 36 * h * wd
-    elif w == "fresnel1024":
+        return plan, run, n_iter, "it/s", 36 * n * n, nm, True
+
+    if w == "gs256":
+        return gs_plain(256, 20, 1001, 1002, 0)
+    if w == "gs2048q4":
+        return gs_plain(2048, 100, 0, 1, 4)
+    if w == "gs4096":
+        return gs_plain(4096, 100, 8001, 8002, 0)
+    if w == "fresnel1024":
         h = wd = 1024
         n_iter = 100
         a = torch.from_numpy(synth.spots_target(h, wd, 50, seed=2001)).to(dev)
@@ -503,8 +573,8 @@ def run_config(args):
                        quant_levels=8)
         nm = torch.zeros((1, n_iter + 1), dtype=torch.float32, device=dev)
         run = lambda: plan.gs([a], n_iter, init_phase=[p0], nmse_out=nm)  # noqa: E731
-        units, unit, bpu = n_iter, "it/s", 36 * h * wd
-    elif w == "mraf2048":
+        return plan, run, n_iter, "it/s", 36 * h * wd, nm, True
+    if w in ("mraf2048", "hio2048"):
         h = wd = 2048
         n_iter = 100
         a = torch.from_numpy(synth.spots_target(h, wd, 50, seed=6001)).to(dev)
@@ -513,21 +583,13 @@ def run_config(args):
         mask[h // 8: 3 * h // 8, wd // 8: 3 * wd // 8] = 1
         plan = hg.Plan([h], [wd])
         nm = torch.zeros((1, n_iter + 1), dtype=torch.float32, device=dev)
-        run = lambda: plan.mraf([a], 0.5, n_iter, signal_mask=[mask], init_phase=[p0], nmse_out=nm)  # noqa: E731
-        units, unit, bpu = n_iter, "it/s", 36 * h * wd
-    elif w == "hio2048":
-        h = wd = 2048
-        n_iter = 100
-        a = torch.from_numpy(synth.spots_target(h, wd, 50, seed=6001)).to(dev)
-        p0 = torch.from_numpy(synth.uniform_phase(h, wd, seed=6002)).to(dev)
-        mask = torch.zeros((h, wd), dtype=torch.uint8, device=dev)
-        mask[h // 8: 3 * h // 8, wd // 8: 3 * wd // 8] = 1
-        plan = hg.Plan([h], [wd])
-        nm = torch.zeros((1, n_iter + 1), dtype=torch.float32, device=dev)
+        if w == "mraf2048":
+            run = lambda: plan.mraf([a], 0.5, n_iter, signal_mask=[mask], init_phase=[p0], nmse_out=nm)  # noqa: E731
+            return plan, run, n_iter, "it/s", 36 * h * wd, nm, True
         run = lambda: plan.hio([a], 0.7, n_iter, signal_mask=[mask], init_phase=[p0], nmse_out=nm)  # noqa: E731
         # GS's 36 B/px plus the stored input X read and written on the noise region
-        units, unit, bpu = n_iter, "it/s", 36 * h * wd + 16 * (h * wd - (h // 4) * (wd // 4))
-    elif w == "dbs128":
+        return plan, run, n_iter, "it/s", 36 * h * wd + 16 * (h * wd - (h // 4) * (wd // 4)), nm, True
+    if w == "dbs128":
         h = wd = 128
         n_sweeps = 2
         a = torch.from_numpy(synth.blur_target(h, wd, SIGMA, seed=7001)).to(dev)
@@ -536,8 +598,8 @@ def run_config(args):
         nm = torch.zeros((1, n_sweeps + 1), dtype=torch.float32, device=dev)
         run = lambda: plan.dbs([a], n_sweeps, init_phase=[p0], nmse_out=nm)  # noqa: E731
         # trial flips; the replay plane stays in registers, so no HBM bytes per trial
-        units, unit, bpu = n_sweeps * h * wd, "trial flips/s", 0
-    else:
+        return plan, run, n_sweeps * h * wd, "trial flips/s", 0, nm, False
+    if w == "ospr":
         h, wd, nt, ns = 1080, 1920, 16, 24
         ts = [torch.from_numpy(synth.symmetrise(synth.blur_target(h, wd, SIGMA, seed=3001 + k))).to(dev)
               for k in range(nt)]
@@ -545,20 +607,28 @@ def run_config(args):
         plan = hg.Plan([h] * nt, [wd] * nt, quant_levels=2)
         nm = torch.zeros((nt, ns), dtype=torch.float32, device=dev)
         run = lambda: plan.ospr(ts, ns, 0, 3000, bits_out=bits, nmse_out=nm)  # noqa: E731
-        units, unit, bpu = nt * ns, "subframes/s", 44 * h * wd
-    if w == "dbs128":
-        pass  # no strip width: one cluster per item
-    elif args.strip_width is None:
-        plan.autotune()  # GS strip widths (OSPR keeps its row-major field)
-    else:
-        plan.set_strip_width(0, args.strip_width)
-    width = plan.strip_width(0)
+        return plan, run, nt * ns, "subframes/s", 44 * h * wd, nm, False
+    raise ValueError(w)
+
+
+def time_workload(w: str, dev, warmup: int, steps: int, strip_width=None, tune=True) -> dict:
+    """Times one configuration over CUDA-graph replays (median of `steps` after `warmup`)."""
+    import torch
+
+    plan, run, units, unit, bpu, nm, tunable = config_workload(w, dev)
+    width = None
+    if tunable:
+        if strip_width is not None:
+            plan.set_strip_width(0, strip_width)
+        elif tune:
+            plan.autotune()  # GS strip widths
+        width = plan.strip_width(0)
     plan.set_graph(True)
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         run()
     torch.cuda.synchronize()
     times = []
-    for _ in range(args.steps):
+    for _ in range(steps):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         run()
@@ -571,15 +641,36 @@ def run_config(args):
     line = {"workload": w, "value": units / (ms / 1e3), "unit": unit, "ms_per_run": ms,
             "alg_bytes_per_unit": bpu, "achieved_gb_s": gbs if bpu else None,
             "frac_of_hbm": gbs / peak if bpu else None, "peak_source": src,
-            "final_nmse": nm.cpu().numpy()[:, -1].tolist()[:4], "steps": args.steps, "warmup": args.warmup,
-            "graph": True}
-    if w != "dbs128":
-        line["strip_width" if args.strip_width is not None else "autotuned_strip_width"] = width
+            "final_nmse": nm.cpu().numpy()[:, -1].tolist()[:4], "steps": steps, "warmup": warmup, "graph": True}
+    if width is not None:
+        line["strip_width" if strip_width is not None else ("autotuned_strip_width" if tune else "strip_width")] = width
     plan.close()
-    print(json.dumps(line))
+    return line
+
+
+def run_config(args):
+    """The remaining single-GPU configurations (see config_workload), each timed over graph replays
+    after warm-up, GS strip widths autotuned first unless --strip-width is given."""
+    import torch
+
+    from __graft_entry__ import build
+
+    build()
+    dev = torch.device("cuda", 0)
+    print(json.dumps(time_workload(args.workload, dev, args.warmup, args.steps, args.strip_width)))
 
 
 def run_gd(args):
+    """Prints gd_vs_gs (below) as one JSON line."""
+    import torch
+
+    from __graft_entry__ import build
+
+    build()
+    print(json.dumps(gd_vs_gs(torch.device("cuda", 0), args.warmup)))
+
+
+def gd_vs_gs(dev, warmup: int) -> dict:
     """Gradient descent vs multi-plane GS, time to a stated NMSE: 2048^2 phase, Fresnel planes at
     z = 0.08, 0.10, 0.12 m (532 nm, 8 um pitch), target intensities = squared spot images (seeds
     4001..4003, unit energy), start phase uniform (seed 4000).  GD: Adam lr 0.05 for up to 200 steps
@@ -591,10 +682,7 @@ def run_gd(args):
 
     import paper_2006_10509_gb300 as hg
     import synth
-    from __graft_entry__ import build
 
-    build()
-    dev = torch.device("cuda", 0)
     n, zs, lam, pitch = 2048, [0.08, 0.10, 0.12], 532e-9, 8e-6
     ts = []
     for p in range(3):
@@ -606,7 +694,7 @@ def run_gd(args):
     steps, iters = 200, 1000
     # gradient descent
     with hg.Plan([n], [n], **kw) as plan:
-        for _ in range(args.warmup):  # warm-up on a scratch copy
+        for _ in range(warmup):  # warm-up on a scratch copy
             ph, m, v = phi0.clone(), torch.zeros_like(phi0), torch.zeros_like(phi0)
             plan.gd_step([ph], ts, [m], [v], 1, 0.05)
         ph, m, v = phi0.clone(), torch.zeros_like(phi0), torch.zeros_like(phi0)
@@ -623,7 +711,7 @@ def run_gd(args):
     # multi-plane GS (same start)
     with hg.Plan([n], [n], **kw) as plan:
         nm = torch.zeros((1, iters + 1), dtype=torch.float32, device=dev)
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             plan.gs(amps, 10, init_phase=[phi0], nmse_out=nm[:, :11])
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -658,7 +746,7 @@ def run_gd(args):
                    "best_nmse": float(gs_nmse.min()), "best_at": int(np.argmin(gs_nmse)),
                    "alg_gb_s": 108 * n * n / (gs_ms / iters / 1e3) / 1e9},
             "curves": {"gd_loss_every_20": gd_loss[::20].tolist(), "gs_nmse_every_100": gs_nmse[::100].tolist()}}
-    print(json.dumps(line))
+    return line
 
 
 def main():
@@ -669,13 +757,13 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-iters", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="gs2048",
-                    choices=["gs2048", "batch", "gd", "gs256", "fresnel1024", "ospr", "mraf2048", "hio2048",
-                             "dbs128"],
+    ap.add_argument("--no-secondary", action="store_true", help="skip the 'secondary' workloads of the headline line")
+    ap.add_argument("--workload", default="gs2048", choices=["gs2048", "batch", "gd", *CONFIG_WORKLOADS],
                     help="gs2048: the headline line; batch: the mixed-size serving batch; "
                          "gd: gradient descent vs multi-plane GS, time to NMSE; gs256 / fresnel1024 / ospr: "
                          "the other single-GPU configurations; mraf2048 / hio2048: the MRAF and HIO variants of GS; "
-                         "dbs128: direct binary search, 128^2, two sweeps")
+                         "dbs128: direct binary search, 128^2, two sweeps; gs2048q4: the headline with 4-level "
+                         "phase; gs4096: GS at 4096^2")
     ap.add_argument("--strip-width", type=int, default=None,
                     help="gs256 / fresnel1024 / mraf2048 / hio2048: use this strip width (-1: the whole run in "
                          "one thread-block cluster) instead of the autotuner's choice")
@@ -688,7 +776,7 @@ def main():
     if args.workload == "gd":
         run_gd(args)
         return
-    if args.workload in ("gs256", "fresnel1024", "ospr", "mraf2048", "hio2048", "dbs128"):
+    if args.workload in CONFIG_WORKLOADS:
         run_config(args)
         return
     if args.impl == "reference":
