@@ -99,3 +99,32 @@ def test_timed_graph_replay_reports_one_replay_and_same_results():
     # one replay: 8 column passes + 8 row passes (+ init, final NMSE pass, finalise, target re-layout)
     assert kt["col_gs"][1] == 8 and kt["row_gs"][1] == 8
     assert all(ms > 0 for ms, _ in kt.values())
+
+
+@pytest.mark.gpu
+def test_batch_with_2048_and_4096_items():
+    """A batch holding the two largest sizes of the mixed-size serving workload (and a 512^2 item):
+    bitwise what one-item plans give, and one teacher-forced 4-level step of each large item
+    against the FP64 oracle."""
+    from oracle import project
+    from tests.helpers import check_levels
+
+    import paper_2006_10509_gb300 as hg
+
+    dev = cuda_device()
+    sizes = [(4096, 4096), (2048, 2048), (512, 512), (2048, 2048)]
+    levels = 4
+    targets = [synth.blur_target(h, w, 2.0, seed=1700 + i) for i, (h, w) in enumerate(sizes)]
+    rng = np.random.default_rng(1800)
+    phases = [(2 * np.pi * rng.integers(0, levels, s) / levels).astype(np.float32) for s in sizes]
+    (outs,), _, _ = _run_plan(hg, dev, sizes, targets, phases, 2, levels)
+    for i in range(3):
+        (single,), _, _ = _run_plan(hg, dev, [sizes[i]], [targets[i]], [phases[i]], 2, levels)
+        assert np.array_equal(single[0][0], outs[0][i]), i
+        assert np.array_equal(single[1][0], outs[1][i]), i
+    (one,), _, _ = _run_plan(hg, dev, sizes, targets, phases, 1, levels)
+    for i in (0, 1):
+        a64 = targets[i].astype(np.float64)
+        h0, _ = project.slm_project(np.exp(1j * phases[i].astype(np.float64)), levels)
+        st = ogs.gs_step(h0, a64, levels)
+        check_levels(one[0][i], st["q"], st["g"], levels)
