@@ -40,8 +40,11 @@
  *  - Device pointers are checked before launch: a pointer that is not device memory of the plan's
  *    device, or a buffer that does not fit in its allocation, is rejected with HG_ERR_INVALID_ARG.
  *  - A plan is used from one host thread at a time.  Different plans are independent.
- *  - Supported FFT lengths (H and W): 8, 16, 32, 64, 128, 256, 512, 1024, 2048, 4096, 12, 15, 30,
- *    60, 120, 864, 1080, 1536, 1920.  Other sizes give HG_ERR_UNSUPPORTED_SIZE.
+ *  - Supported FFT lengths (H and W): every n = 2^a 3^b 5^c with 1 <= n <= 4096 (137 lengths).
+ *    8, 16, 32, 64, 128, 256, 512, 1024, 2048, 4096, 12, 15, 30, 60, 120, 864, 1080, 1536 and 1920
+ *    have compiled kernels (radix plans fixed at build time, the field in registers between
+ *    stages); the others run on generic kernels (a run-time radix plan, the tile in shared memory
+ *    between stages; slower, same arithmetic).  Other sizes give HG_ERR_UNSUPPORTED_SIZE.
  */
 #ifndef HOLOGEN_H
 #define HOLOGEN_H
@@ -298,11 +301,19 @@ HG_API hg_status hg_gd_backward(hg_plan* plan, float* const* phase, const float*
  *  - Limits: height * width <= 1048576 pixels, each a supported FFT length; larger sizes return
  *    HG_ERR_UNSUPPORTED_SIZE before anything is launched.
  *  - The first call on a device looks up the array's device address (cudaGetSymbolAddress), so make
- *    that first call before any stream capture.
+ *    that first call before any stream capture.  The address is looked up again whenever the
+ *    calling thread's current context is a different one from the last lookup's (for example after
+ *    cudaDeviceReset, which unloads the module holding the array).
+ *  - Under CUDA's default lazy module loading the driver loads the module that holds the array, and
+ *    reserves the array, during the first call on a device, and loads each FFT length's kernels at
+ *    their first launch.  Callers that must not allocate after start-up should make one warm-up
+ *    call per device and per (height, width) at start-up, or run with CUDA_MODULE_LOADING=EAGER.
  *  - Calls no cudaMalloc / cudaFree or allocating routine.  Every call shares the one array and
  *    leaves its contents behind; each call rewrites the tables and every partial it reads on its own
- *    stream before using them, so nothing has to start at zero.  Calls that overlap on the GPU (different streams, other host threads)
- *    race on the array and give wrong results: serialise them.
+ *    stream before using them, so nothing has to start at zero.  Any two calls that are not ordered
+ *    on one stream race on the array and give wrong results -- calls from other host threads, and
+ *    calls from the same thread on two different streams alike: the caller serialises them (one
+ *    stream, or an event and a stream wait between them).
  */
 HG_API hg_status hg_gs_run_noalloc(int32_t height, int32_t width, int32_t quant_levels, const float* target_amp,
                                    const float* init_phase, uint64_t seed, int32_t n_iter, float* phase_out,
@@ -369,7 +380,7 @@ HG_API const char* hg_status_string(hg_status status);
 /* Detail message of the last failing call on this host thread ("" if none). */
 HG_API const char* hg_last_error(void);
 
-/* 1 if n is a supported FFT length, else 0. */
+/* 1 if n is a supported FFT length (n = 2^a 3^b 5^c, 1 <= n <= 4096), else 0. */
 HG_API int32_t hg_supported_length(int32_t n);
 
 #ifdef __cplusplus

@@ -81,13 +81,48 @@ __global__ void k_noalloc_tables(const hg::TwiddleLayout tw_w, const hg::Twiddle
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 unsigned char* g_base[kMaxDevices] = {};
+unsigned long long g_ctx_id[kMaxDevices] = {};  // driver ID of the context g_base[dev] belongs to
 
 hg_status err(hg_status s, const char* m) {
   hg::set_last_error(m);
   return s;
 }
 
-// Device address of g_scratch on the current device, looked up once per device.
+// cuCtxGetCurrent and cuCtxGetId from the driver, looked up at run time (the library does not link
+// libcuda).  A context's ID is unique for the life of the process, unlike its handle, which a new
+// context may reuse after the old one is destroyed.
+typedef int (*ctx_current_fn_t)(void**);
+typedef int (*ctx_id_fn_t)(void*, unsigned long long*);
+struct CtxFns {
+  ctx_current_fn_t current = nullptr;
+  ctx_id_fn_t id = nullptr;
+};
+const CtxFns& ctx_fns() {
+  static const CtxFns f = [] {
+    CtxFns x;
+    if (void* h = dlopen("libcuda.so.1", RTLD_NOW | RTLD_LOCAL)) {
+      x.current = (ctx_current_fn_t)dlsym(h, "cuCtxGetCurrent");
+      x.id = (ctx_id_fn_t)dlsym(h, "cuCtxGetId");
+    }
+    return x;
+  }();
+  return f;
+}
+
+// ID of the calling thread's current context, or 0 when it cannot be told.
+unsigned long long current_ctx_id() {
+  const CtxFns& f = ctx_fns();
+  void* ctx = nullptr;
+  unsigned long long id = 0;
+  if (!f.current || !f.id || f.current(&ctx) != 0 || !ctx || f.id(ctx, &id) != 0) return 0;
+  return id;
+}
+
+// Device address of g_scratch in the current device's context.  It is looked up with
+// cudaGetSymbolAddress the first time and again whenever the current context is not the one the
+// cached address belongs to (the module holding g_scratch is loaded anew in a new context, e.g.
+// after cudaDeviceReset, and the array may then sit elsewhere); where the driver cannot name the
+// context the lookup is made on every call.
 hg_status scratch_base(unsigned char** out) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
@@ -95,7 +130,8 @@ hg_status scratch_base(unsigned char** out) {
     return err(HG_ERR_CUDA, "no usable current CUDA device");
   }
   std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_base[dev]) {
+  const unsigned long long id = current_ctx_id();
+  if (!g_base[dev] || id == 0 || id != g_ctx_id[dev]) {
     void* ptr = nullptr;
     const cudaError_t e = cudaGetSymbolAddress(&ptr, g_scratch);
     if (e != cudaSuccess || !ptr) {
@@ -103,6 +139,8 @@ hg_status scratch_base(unsigned char** out) {
       return err(HG_ERR_CUDA, "cudaGetSymbolAddress(g_scratch) failed");
     }
     g_base[dev] = static_cast<unsigned char*>(ptr);
+    // the lookup makes the device's primary context current if nothing was: take its ID now
+    g_ctx_id[dev] = current_ctx_id();
   }
   *out = g_base[dev];
   return HG_OK;
@@ -202,6 +240,8 @@ extern "C" hg_status hg_gs_run_noalloc(int32_t height, int32_t width, int32_t qu
   a.field = reinterpret_cast<float2*>(base);
   a.partials = reinterpret_cast<float2*>(base + kOffPartials);
   a.col_blocks = col_blocks;
+  if (rk->gen) a.gen_row = *rk->gen;
+  if (ck->gen) a.gen_col = *ck->gen;
   a.nmse = nmse_out;
   a.seed = seed;
   a.target[0] = target_amp;
