@@ -1,6 +1,7 @@
 """Builds libhologen.so in-tree with nvcc for sm_103a (no CMake, no torch extension machinery).
 
-Each supported FFT length is one translation unit (csrc/hg_len.cu with -DHG_LEN=N); the C ABI is
+Each FFT length with a compiled instance is one translation unit (csrc/hg_len.cu with -DHG_LEN=N);
+the generic kernels of every other {2,3,5}-smooth length are csrc/hg_gen.cu; the C ABI is
 csrc/hg_api.cu.  Objects go to paper_2006_10509_gb300/_build/, the library to
 paper_2006_10509_gb300/libhologen.so.  Translation units compile in parallel and are rebuilt only
 when a source or header is newer than the object.
@@ -65,6 +66,7 @@ def build(verbose: bool = False, jobs: int | None = None) -> str:
     units.append((os.path.join(CSRC, "hg_api.cu"), os.path.join(BUILD, "hg_api.o"), []))
     units.append((os.path.join(CSRC, "hg_noalloc.cu"), os.path.join(BUILD, "hg_noalloc.o"), []))
     units.append((os.path.join(CSRC, "hg_dbs.cu"), os.path.join(BUILD, "hg_dbs.o"), []))
+    units.append((os.path.join(CSRC, "hg_gen.cu"), os.path.join(BUILD, "hg_gen.o"), []))
     todo = [u for u in units if not os.path.exists(u[1]) or os.path.getmtime(u[1]) < newest]
     jobs = jobs or max(1, min(len(todo), os.cpu_count() or 4))
     logs = []

@@ -28,6 +28,8 @@
 
 namespace hg {
 
+// The compiled instance of a length, else the generic kernels (any n = 2^a 3^b 5^c up to
+// kGenMaxLength), else nullptr.
 const RowKernels* row_kernels(int n) {
   switch (n) {
 #define HG_CASE(N) \
@@ -36,7 +38,7 @@ const RowKernels* row_kernels(int n) {
     HG_FOR_EACH_LENGTH(HG_CASE)
 #undef HG_CASE
     default:
-      return nullptr;
+      return gen_row_kernels(n);
   }
 }
 
@@ -48,7 +50,7 @@ const ColKernels* col_kernels(int n) {
     HG_FOR_EACH_LENGTH(HG_CASE)
 #undef HG_CASE
     default:
-      return nullptr;
+      return gen_col_kernels(n);
   }
 }
 
@@ -119,6 +121,7 @@ struct SizeClass {
   float* ttile = nullptr;        // [slot][plane][strip][H][C] targets re-laid out for the GS column passes
   float2* hio = nullptr;         // [slot][strip][H][C] HIO replay-plane input (allocated on first use)
   double* stats = nullptr;       // [slot][plane][4] gradient-descent loss statistics
+  float2* gacc = nullptr;        // [slot][H][W] generic-length multi-plane accumulator (first use)
   std::vector<float2*> cx, cy;   // per plane (Fresnel)
   int row_blocks() const { return (H + rk->rows - 1) / rk->rows; }
   int col_blocks() const { return (W + ck->cols - 1) / ck->cols; }    // strips on a row-major field
@@ -467,6 +470,8 @@ void fill_common(const hg_plan* p, const SizeClass& c, int plane, hg::PassArgs& 
   }
   a.stats = c.stats;
   a.centred = p->centred ? 1 : 0;
+  if (c.rk->gen) a.gen_row = *c.rk->gen;
+  if (c.ck->gen) a.gen_col = *c.ck->gen;
 }
 
 }  // namespace
@@ -515,6 +520,37 @@ namespace {
 
 // items per launch: (item, plane) pairs of one launch must fit the argument block
 int chunk_items(const hg_plan* p) { return std::max(1, hg::kMaxBatch / p->P); }
+
+// Grid of the generic multi-plane pointwise kernels: a grid-stride loop over one item's field per
+// blockIdx.y.
+dim3 pointwise_grid(const SizeClass& c, int nb) {
+  const int64_t blocks = ((int64_t)c.H * c.W + 255) / 256;
+  return dim3((unsigned)std::min<int64_t>(blocks, 4 * 152), (unsigned)nb);
+}
+
+// Generic row lengths: the multi-plane accumulator of a class, allocated on first use.
+hg_status ensure_plane_acc(hg_plan* p, SizeClass& c) {
+  if (!c.rk->gen || c.gacc) return HG_OK;
+  return p->alloc(&c.gacc, c.items.size() * (size_t)c.H * c.W, "multi-plane accumulator");
+}
+
+// Generic row lengths: every plane's forward row FFTs of the accumulator c_p -> field p.
+hg_status plane_forwards(hg_plan* p, const SizeClass& c, int kind, const hg::PassArgs& a, dim3 grow, cudaStream_t st) {
+  hg_status s;
+  for (int q = 0; q < p->P; ++q)
+    if ((s = launch(p, kind, c.rk->plane.fwd, grow, c.rk->nt, c.rk->smem, a, st, q, (float*)c.gacc)) != HG_OK)
+      return s;
+  return HG_OK;
+}
+
+// Generic row lengths: the sum over planes of conj(c_p) (inverse row FFTs of field p) -> accumulator.
+hg_status plane_backs(hg_plan* p, const SizeClass& c, int kind, const hg::PassArgs& a, dim3 grow, cudaStream_t st) {
+  hg_status s;
+  for (int q = 0; q < p->P; ++q)
+    if ((s = launch(p, kind, c.rk->plane.back, grow, c.rk->nt, c.rk->smem, a, st, q, (float*)c.gacc)) != HG_OK)
+      return s;
+  return HG_OK;
+}
 
 }  // namespace
 
@@ -895,9 +931,18 @@ hg_status gs_class(hg_plan* p, const SizeClass& c, const GsCall& g, cudaStream_t
         }
       }
       const dim3 gfin(1, nb);
+      const bool gen = c.rk->gen != nullptr;  // generic row length: one launch per plane
+      float* acc = (float*)c.gacc;
       if ((s = launch(p, K_AMP_ENERGY, (const void*)&k_amp_energy, gcol, 256, 0, a, st)) != HG_OK) return s;
       if ((s = launch(p, K_FINALIZE, (const void*)&hg::k_finalize<2>, gfin, 32, 0, a, st)) != HG_OK) return s;
-      if ((s = launch(p, K_ROW_MP_INIT, c.rk->mp_init[1], grow, c.rk->nt, c.rk->smem, a0, st)) != HG_OK) return s;
+      if (gen) {
+        if ((s = launch(p, K_ROW_MP_INIT, c.rk->plane.start[1], pointwise_grid(c, nb), 256, 0, a0, st, 0, acc)) !=
+                HG_OK ||
+            (s = plane_forwards(p, c, K_ROW_MP_INIT, a, grow, st)) != HG_OK)
+          return s;
+      } else if ((s = launch(p, K_ROW_MP_INIT, c.rk->mp_init[1], grow, c.rk->nt, c.rk->smem, a0, st)) != HG_OK) {
+        return s;
+      }
       for (int it = 0; it < n_iter; ++it) {
         a.iter = it;
         if ((s = launch(p, K_COL_GS, c.ck->gs[1][0], gcol, c.ck->nt, c.ck->smem_gs, a, st)) != HG_OK) return s;
@@ -905,7 +950,14 @@ hg_status gs_class(hg_plan* p, const SizeClass& c, const GsCall& g, cudaStream_t
         hg::PassArgs ar = last ? ao : a;
         ar.finalize = nmse_out != nullptr;
         ar.fin_iter = it;
-        if ((s = launch(p, K_ROW_MP, c.rk->mp[last], grow, c.rk->nt, c.rk->smem, ar, st)) != HG_OK) return s;
+        if (gen) {
+          if ((s = plane_backs(p, c, K_ROW_MP, ar, grow, st)) != HG_OK ||
+              (s = launch(p, K_ROW_MP, c.rk->plane.project, pointwise_grid(c, nb), 256, 0, ar, st, 0, acc)) != HG_OK ||
+              (s = plane_forwards(p, c, K_ROW_MP, a, grow, st)) != HG_OK)
+            return s;
+        } else if ((s = launch(p, K_ROW_MP, c.rk->mp[last], grow, c.rk->nt, c.rk->smem, ar, st)) != HG_OK) {
+          return s;
+        }
       }
       a.iter = n_iter;
       a.fin_iter = n_iter;
@@ -1204,6 +1256,9 @@ hg_status hg_gs_run(hg_plan* p, const float* const* target_amp, const float* con
   if (nmse_out && (s = check_ptr(p, nmse_out, (size_t)p->n_items * (n_iter + 1) * 4, 4, "nmse_out", 0)) != HG_OK)
     return s;
 
+  if (p->P > 1)
+    for (SizeClass& c : p->classes)
+      if ((s = ensure_plane_acc(p, c)) != HG_OK) return s;
   const GsCall call{target_amp, init_phase, seed, n_iter, phase_out, level_out, nmse_out};
   std::vector<uintptr_t> key{1, (uintptr_t)n_iter, (uintptr_t)seed, (uintptr_t)nmse_out};
   if (p->graph)
@@ -1635,6 +1690,8 @@ static hg_status gd_run(hg_plan* p, float* const* phase, const float* const* tar
   }
   if (loss_out && (s = check_ptr(p, loss_out, (size_t)p->n_items * (P + 1) * 4, 4, "loss_out", 0)) != HG_OK) return s;
   if (grad_scale && (s = check_ptr(p, grad_scale, 4, 4, "grad_scale", 0)) != HG_OK) return s;
+  for (SizeClass& c : p->classes)
+    if ((s = ensure_plane_acc(p, c)) != HG_OK) return s;
 
   cudaStream_t st = (cudaStream_t)stream;
   const int chunk = chunk_items(p);
@@ -1667,14 +1724,29 @@ static hg_status gd_run(hg_plan* p, float* const* phase, const float* const* tar
         a.grad[k] = grad_out ? grad_out[item] : nullptr;
       }
       const dim3 grow(c.row_blocks(), nb), gcol(c.col_blocks(), nb * P);
+      const bool gen = c.rk->gen != nullptr;  // generic row length: one launch per plane
       if (fwd) {
-        if ((s = launch(p, K_ROW_GD_FWD, c.rk->mp_init[0], grow, c.rk->nt, c.rk->smem, a, st)) != HG_OK) return s;
+        if (gen) {
+          if ((s = launch(p, K_ROW_GD_FWD, c.rk->plane.start[0], pointwise_grid(c, nb), 256, 0, a, st, 0,
+                          (float*)c.gacc)) != HG_OK ||
+              (s = plane_forwards(p, c, K_ROW_GD_FWD, a, grow, st)) != HG_OK)
+            return s;
+        } else if ((s = launch(p, K_ROW_GD_FWD, c.rk->mp_init[0], grow, c.rk->nt, c.rk->smem, a, st)) != HG_OK) {
+          return s;
+        }
         if ((s = launch(p, K_COL_GD_FWD, c.ck->gd[0], gcol, c.ck->nt, c.ck->smem, a, st)) != HG_OK) return s;
         if ((s = launch(p, K_FINALIZE, (const void*)&hg::k_finalize<1>, dim3(1, nb), 32, 0, a, st)) != HG_OK) return s;
       }
       if (bwd) {
         if ((s = launch(p, K_COL_GD_BWD, c.ck->gd[1], gcol, c.ck->nt, c.ck->smem, a, st)) != HG_OK) return s;
-        if ((s = launch(p, K_ROW_GD_BWD, c.rk->gd_bwd, grow, c.rk->nt, c.rk->smem, a, st)) != HG_OK) return s;
+        if (gen) {
+          if ((s = plane_backs(p, c, K_ROW_GD_BWD, a, grow, st)) != HG_OK ||
+              (s = launch(p, K_ROW_GD_BWD, c.rk->plane.grad, pointwise_grid(c, nb), 256, 0, a, st, 0,
+                          (float*)c.gacc)) != HG_OK)
+            return s;
+        } else if ((s = launch(p, K_ROW_GD_BWD, c.rk->gd_bwd, grow, c.rk->nt, c.rk->smem, a, st)) != HG_OK) {
+          return s;
+        }
       }
     }
   }

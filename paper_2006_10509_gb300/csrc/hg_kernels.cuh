@@ -18,6 +18,7 @@
 #include <type_traits>
 
 #include "hg_fft.cuh"
+#include "hg_launch.h"
 
 namespace hg {
 
@@ -231,6 +232,8 @@ struct PassArgs {
   const float* grad_scale;             // device scalar multiplying the gradient, or nullptr (= 1)
   int adam;                            // 1: apply the Adam update
   float lr, beta1, beta2, eps, bc1, bc2;  // Adam; bc1 = 1 - beta1^t, bc2 = 1 - beta2^t
+  // generic kernels (lengths without a compiled instance): the run-time plans of W and H
+  GenPlan gen_row, gen_col;
 };
 
 // ---------------------------------------------------------------- pointwise pieces

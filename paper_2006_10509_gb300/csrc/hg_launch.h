@@ -13,6 +13,22 @@ struct TwiddleLayout {
   int ns[16], r[16], off[16];
 };
 
+// Run-time radix plan of the generic kernels (lengths without a compile-time instance): stage s has
+// radix r[s] after ns[s] = r[0] ... r[s-1] points and reads its twiddles w_{ns R}^{q k} at
+// tw + off[s] + (q - 1) ns + k (off[s] < 0 for the first stage, which needs none; the tables of the
+// later stages follow one another).  The stages are n16 radix-16 ones, one radix-r2 one (r2 = 8, 4,
+// 2, or 0 for none), n9 radix-9, n3 (0 or 1) radix-3 and n5 radix-5 ones, in that order: the device
+// code runs from these counts, the arrays serve the host.  batch: rows of a row tile, or columns of
+// a column strip, per CTA.
+constexpr int kGenMaxStages = 12;
+struct GenPlan {
+  int n;
+  int batch;
+  int stages;
+  int n16, r2, n9, n3, n5;
+  int r[kGenMaxStages], ns[kGenMaxStages], off[kGenMaxStages];
+};
+
 struct RowKernels {
   int rows;      // rows per CTA
   int nt;        // threads per CTA
@@ -32,12 +48,23 @@ struct RowKernels {
   const void* mp_init[2];   // k_row_mp_init<PROJECT = false (gradient descent) / true (GS)>
   const void* mp[2];        // k_row_mp<OUT = false / true>
   const void* gd_bwd;       // k_row_gd_bwd
+  // generic lengths only (mp_init / mp / gd_bwd are nullptr there): multi-plane GS and gradient
+  // descent run one launch per plane through a plan-owned accumulator [slot][H][W] complex64;
+  // kernels (PassArgs, int plane, float* accumulator)
+  struct Plane {
+    const void* start[2];   // h_0 into the accumulator: [0] exp(i phi) (GD), [1] P_SLM(exp(i phi)) (GS)
+    const void* fwd;        // plane p: accumulator c_p -> forward row FFTs -> field p
+    const void* back;       // plane p: conj(c_p) inverse row FFTs of field p -> accumulator (+=)
+    const void* project;    // accumulator -> P_SLM(accumulator), outputs
+    const void* grad;       // gradient and Adam from the accumulator
+  } plane;
   // GS with the whole run in one thread-block cluster per N x N item (k_gs_cluster; nullptr where
   // not instantiated): [0] clusters of 8 CTAs, [1] of 16
   const void* gs_cluster[2];
   int nt_cluster[2], smem_cluster[2];
   void (*set_attrs)();      // raises the dynamic shared-memory limit on the current device
   TwiddleLayout tw;         // twiddle tables of length W
+  const GenPlan* gen;       // generic kernels: their run-time plan (nullptr for compiled lengths)
 };
 
 struct ColKernels {
@@ -59,6 +86,7 @@ struct ColKernels {
   const void* gd[2];        // k_col_gd<BWD = false / true>
   void (*set_attrs)();
   TwiddleLayout tw;         // twiddle tables of length H
+  const GenPlan* gen;       // generic kernels: their run-time plan (nullptr for compiled lengths)
 };
 
 // X-macro of every supported FFT length (rows and columns).
@@ -75,6 +103,12 @@ HG_FOR_EACH_LENGTH(HG_DECLARE_LEN)
 // nullptr when the length is not supported
 const RowKernels* row_kernels(int n);
 const ColKernels* col_kernels(int n);
+
+// The generic kernels' tables for a length that has no compiled instance: every n = 2^a 3^b 5^c
+// with 1 <= n <= kGenMaxLength (nullptr otherwise).  Built on first use and kept for the process.
+constexpr int kGenMaxLength = 4096;
+const RowKernels* gen_row_kernels(int n);
+const ColKernels* gen_col_kernels(int n);
 
 // Sets the detail string returned by hg_last_error() on this host thread.
 void set_last_error(const char* msg);

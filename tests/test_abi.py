@@ -42,15 +42,28 @@ def test_status_strings_and_lengths(hg):
     assert hg.hg_status_string(99) == "HG_ERR_UNKNOWN"
     for n in (8, 16, 256, 1080, 1920, 2048, 4096, 15, 864):
         assert hg.hg_supported_length(n)
-    for n in (0, 1, 7, 100, 8192, -4):
+    for n in (0, 7, 4097, 8192, -4, 14, 4095):
         assert not hg.hg_supported_length(n)
+
+
+def test_supported_lengths_are_every_235_smooth_length_up_to_4096(hg):
+    # compiled instances and the generic kernels together: exactly n = 2^a 3^b 5^c, 1 <= n <= 4096
+    def smooth(n):
+        for p in (2, 3, 5):
+            while n % p == 0:
+                n //= p
+        return n == 1
+
+    got = [n for n in range(0, 4200) if hg.hg_supported_length(n)]
+    want = [n for n in range(1, 4097) if smooth(n)]
+    assert got == want and len(want) == 137
 
 
 @pytest.mark.parametrize(
     "kwargs, status",
     [
         (dict(heights=[], widths=[]), 1),
-        (dict(heights=[64], widths=[100]), 2),
+        (dict(heights=[64], widths=[112]), 2),
         (dict(heights=[7], widths=[64]), 2),
         (dict(heights=[64], widths=[64], propagation=5), 1),
         (dict(heights=[64], widths=[64], quant_levels=1), 1),

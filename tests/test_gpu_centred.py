@@ -42,7 +42,8 @@ def _gs(hg, dev, a, flags, levels, kw, mode=None, mask=None):
 
 @pytest.mark.gpu
 @pytest.mark.parametrize("h, w, levels, fresnel", [(512, 512, 0, False), (2048, 2048, 0, False), (256, 256, 4, True),
-                                                    (1080, 1920, 4, True), (15, 16, 2, False), (120, 64, 0, True)])
+                                                    (1080, 1920, 4, True), (15, 16, 2, False), (120, 64, 0, True),
+                                                    (27, 125, 4, False), (75, 90, 0, True)])
 def test_centred_gs_equals_shifted_plain(h, w, levels, fresnel):
     import paper_2006_10509_gb300 as hg
 

@@ -65,7 +65,7 @@ def _replay_check(a, phi0, q1, c):
 
 @pytest.mark.gpu
 @pytest.mark.parametrize("h, w, z", [(32, 32, None), (64, 64, None), (64, 128, None), (128, 128, None),
-                                     (64, 64, 0.02), (120, 64, None)])
+                                     (64, 64, 0.02), (120, 64, None), (36, 50, None), (45, 27, 0.02)])
 def test_dbs_one_sweep_follows_the_oracle(h, w, z):
     import paper_2006_10509_gb300 as hg
 

@@ -68,6 +68,8 @@ CASES = [
     (512, 512, 2, 0.5, None),
     (2048, 1024, 0, 0.9, None),
     (1080, 1920, 4, 0.7, 0.1),
+    (360, 480, 0, 0.7, None),
+    (90, 100, 4, 0.7, 0.05),
 ]
 
 

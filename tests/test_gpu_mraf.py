@@ -59,6 +59,8 @@ CASES = [
     (512, 512, 2, 0.8, None),
     (2048, 1024, 0, 0.6, None),
     (1080, 1920, 4, 0.5, 0.1),
+    (360, 480, 0, 0.6, None),
+    (90, 100, 4, 0.5, 0.05),
 ]
 
 

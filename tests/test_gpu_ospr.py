@@ -33,7 +33,7 @@ def _run(hg, dev, targets, s, n_iter=0, seed=3000, z=None):
 
 @pytest.mark.gpu
 @pytest.mark.parametrize("h, w, s, z", [(64, 64, 4, None), (30, 120, 3, None), (120, 64, 3, 0.05),
-                                        (1080, 1920, 3, None)])
+                                        (1080, 1920, 3, None), (90, 120, 3, None), (100, 75, 2, 0.05)])
 def test_ospr_subframes_match_oracle(h, w, s, z):
     import paper_2006_10509_gb300 as hg
 

@@ -1,7 +1,8 @@
 """GPU parity of the bare Fourier / Fresnel transforms (hg_propagate) against the FP64 oracle.
 
 Sizes span one tile, several tiles, ragged tails (widths not a multiple of the column strip, heights
-not a multiple of the row tile), mixed radices and the largest supported lengths.  Bar: relative L2
+not a multiple of the row tile), mixed radices and the largest supported lengths, and lengths that run
+on the generic kernels (any 2^a 3^b 5^c up to 4096, down to length 1).  Bar: relative L2
 error <= 1e-4 on identical inputs.
 """
 import numpy as np
@@ -13,7 +14,11 @@ from tests.helpers import FIELD_TOL, cuda_device, rel_l2
 LAM, PITCH = 532e-9, 8e-6
 
 SIZES = [(8, 8), (16, 32), (64, 64), (256, 256), (12, 15), (30, 60), (120, 64), (15, 8), (60, 1920),
-         (864, 1536), (1080, 1920), (2048, 2048), (4096, 256), (512, 4096)]
+         (864, 1536), (1080, 1920), (2048, 2048), (4096, 256), (512, 4096),
+         # lengths without a compiled instance (the generic kernels), alone and mixed with compiled ones:
+         # common SLM sizes, odd and degenerate sizes, the longest generic lengths
+         (1024, 1280), (720, 1280), (2160, 3840), (1000, 1200), (1, 1), (1, 8), (3, 5), (27, 125),
+         (243, 100), (2, 4000), (4050, 6), (3125, 18)]
 
 
 def _field(h, w, seed):
