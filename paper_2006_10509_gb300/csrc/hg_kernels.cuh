@@ -278,6 +278,20 @@ __device__ __forceinline__ float2 slm_project(float2 g, int n_levels, const floa
     q = (g.x < 0.f || (g.x == 0.f && g.y > 0.f)) ? 1 : 0;
     return make_float2(q ? -1.f : 1.f, 0.f);
   }
+  if (n_levels == 4) {
+    // levels 0, pi/2, pi, 3pi/2: the sector of g from |x| against |y| and the signs, no arctangent
+    // (measured on GB300: the 4-level GS row pass at 2048^2 29.8 -> 26.3 us).  A midpoint goes to
+    // the higher index: arg pi/4 -> 1, 3pi/4 -> 2, 5pi/4 -> 3, 7pi/4 -> 0.
+    const float ax = fabsf(g.x), ay = fabsf(g.y);
+    int qq;
+    if (ax > ay || (ax == ay && ((g.x > 0.f) != (g.y > 0.f))))
+      qq = g.x >= 0.f ? 0 : 2;
+    else
+      qq = g.y > 0.f ? 1 : 3;
+    if (ax == 0.f && ay == 0.f) qq = 0;
+    q = qq;
+    return __ldg(&lev[qq]);
+  }
   const float a = atan2f(g.y, g.x);  // (-pi, pi]
   float t = a * ((float)n_levels * 0.15915494309189533577f);
   if (t < 0.f) t += (float)n_levels;
