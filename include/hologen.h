@@ -352,9 +352,11 @@ HG_API hg_status hg_plan_set_graph(hg_plan* plan, int32_t enabled);
  * keeps its field tiled in column strips so that a column pass reads its strip as one contiguous
  * block; the strip width trades the column pass's CTA size against the row pass's access pattern.
  * The plan starts from a measured default per column length.  hg_plan_autotune times, for every
- * size class, a 6-iteration GS run (seeded start, zero target in its own scratch) with each width
- * the class allows (2, 4, 8 or 16 columns, or a row-major field) and keeps the fastest; choices
- * are cached per process by (device, H, W, items in the class, levels, propagation).  It
+ * size class, a 10-iteration GS run (seeded start, zero target in its own scratch; the fastest of
+ * five runs) with each width
+ * the class allows (2, 4, 8 or 16 columns, or a row-major field) and each radix plan of the row and
+ * column passes (below) and keeps the fastest; choices are cached per process by (device, H, W,
+ * items in the class, levels, propagation).  It
  * synchronises `stream` before and after, allocates and frees one scratch target per class, does
  * not count or time its own launches, and drops captured graphs.  Results of later runs do not
  * depend on the width except for the order in which NMSE partial sums are added.
@@ -372,6 +374,22 @@ HG_API hg_status hg_plan_set_graph(hg_plan* plan, int32_t enabled);
 HG_API hg_status hg_plan_autotune(hg_plan* plan, void* stream);
 HG_API hg_status hg_plan_strip_width(const hg_plan* plan, int32_t item, int32_t* width_out);
 HG_API hg_status hg_plan_set_strip_width(hg_plan* plan, int32_t item, int32_t width);
+
+/*
+ * Radix plans (part of the same autotuner; no counterpart in the paper, whose FFT handler defers to
+ * cuFFT's own planning).  Lengths 864, 1024, 1080, 1536, 1920 and 2048 have their single-plane
+ * tiled GS passes compiled with two radix plans: the default (e.g. 2048 = 16 x 16 x 8) and an
+ * alternative (2048 = 16 x 8 x 16; 1024 = 4 x 16 x 16; 864 = 9 x 6 x 16; 1080 = 15 x 9 x 8;
+ * 1536 = 16 x 6 x 16; 1920 = 15 x 8 x 16).  Row and column passes choose independently: plan 0 the
+ * default, 1 the alternative.  hg_plan_autotune times every (strip width, row plan, column plan)
+ * the class allows and keeps the fastest; hg_plan_radix_plan returns the choice of an item's size
+ * class and hg_plan_set_radix_plan sets it by hand (HG_ERR_INVALID_ARG for 1 on a length without
+ * an alternative; synchronises the device and drops captured graphs).  The alternative applies to
+ * plain GS runs on a tiled field (not row-major, cluster, MRAF, HIO, illumination or level-table
+ * runs, which use the default plan).  Results differ between plans only by float32 rounding.
+ */
+HG_API hg_status hg_plan_radix_plan(const hg_plan* plan, int32_t item, int32_t* row_plan, int32_t* col_plan);
+HG_API hg_status hg_plan_set_radix_plan(hg_plan* plan, int32_t item, int32_t row_plan, int32_t col_plan);
 HG_API hg_status hg_plan_item_latency(hg_plan* plan, double* ms_out);
 
 /* Human-readable name of a status code (static string). */

@@ -100,6 +100,9 @@ _SIGNATURES = {
     "hg_plan_autotune": (ctypes.c_int, [_VP, _VP]),
     "hg_plan_strip_width": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
     "hg_plan_set_strip_width": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32]),
+    "hg_plan_radix_plan": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                                          ctypes.POINTER(ctypes.c_int32)]),
+    "hg_plan_set_radix_plan": (ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
     "hg_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "hg_last_error": (ctypes.c_char_p, []),
     "hg_supported_length": (ctypes.c_int32, [ctypes.c_int32]),
@@ -373,6 +376,17 @@ def hg_plan_strip_width(plan: int, item: int) -> int:
     return out.value
 
 
+def hg_plan_radix_plan(plan: int, item: int) -> tuple[int, int]:
+    r = ctypes.c_int32(0)
+    c = ctypes.c_int32(0)
+    _check(load().hg_plan_radix_plan(plan, item, ctypes.byref(r), ctypes.byref(c)), "hg_plan_radix_plan")
+    return r.value, c.value
+
+
+def hg_plan_set_radix_plan(plan: int, item: int, row_plan: int, col_plan: int):
+    _check(load().hg_plan_set_radix_plan(plan, item, row_plan, col_plan), "hg_plan_set_radix_plan")
+
+
 def hg_plan_set_strip_width(plan: int, item: int, width: int):
     _check(load().hg_plan_set_strip_width(plan, item, width), "hg_plan_set_strip_width")
 
@@ -481,6 +495,13 @@ class Plan:
 
     def strip_width(self, item: int) -> int:
         return hg_plan_strip_width(self.handle, item)
+
+    def radix_plan(self, item: int) -> tuple[int, int]:
+        """(row plan, column plan) of the item's size class: 0 default, 1 alternative."""
+        return hg_plan_radix_plan(self.handle, item)
+
+    def set_radix_plan(self, item: int, row_plan: int, col_plan: int):
+        hg_plan_set_radix_plan(self.handle, item, row_plan, col_plan)
 
     def set_strip_width(self, item: int, width: int):
         hg_plan_set_strip_width(self.handle, item, width)

@@ -7,6 +7,7 @@
 #include <dlfcn.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -128,6 +129,10 @@ struct SizeClass {
   // strip width of the tiled GS field (0: single-plane GS keeps the field row-major; -1: GS runs
   // in the whole-run cluster kernel); the default rule at plan creation, or the autotuner's choice
   int tile = 0;
+  // radix plan of the tiled GS passes, per pass: 0 the length's default plan, 1 its alternative
+  // (PlanV); the autotuner's choice, or set by hand.  Used where the width's kernels exist with that
+  // plan and the run takes the plain kernels (not MRAF / HIO / illumination / a level table).
+  int pv_row = 0, pv_col = 0;
   // sizes covering any strip width (the narrowest tiled one is 2): partial sums per strip, and the
   // strips x H x width target copies
   size_t max_strips() const { return (size_t)std::max(col_blocks(), (W + 1) / 2); }
@@ -184,6 +189,7 @@ struct hg_plan {
   std::vector<SizeClass> classes;
   std::vector<int> item_class, item_slot;
   std::map<int, float2*> tw;
+  std::map<int, float2*> tw_alt;  // twiddle tables of the alternative radix plans, per length
   std::map<int, float2*> roots;  // direct binary search: exp(-2 pi i j / N), j < N, per length
   float2* lev = nullptr;
   float* lev_phase = nullptr;
@@ -736,6 +742,10 @@ hg_status hg_plan_create(const hg_plan_desc* d, hg_plan** out) {
       float2* t = nullptr;
       if ((s = upload(p, &t, twiddles(hg::row_kernels(len)->tw), "twiddle table")) != HG_OK) return bail(s);
       p->tw[len] = t;
+      if (hg::row_kernels(len)->has_alt) {
+        if ((s = upload(p, &t, twiddles(hg::row_kernels(len)->tw_alt), "twiddle table")) != HG_OK) return bail(s);
+        p->tw_alt[len] = t;
+      }
     }
   }
   // level tables exp(2 pi i q / N) and 2 pi q / N, exact on the axes
@@ -976,16 +986,21 @@ hg_status gs_class(hg_plan* p, const SizeClass& c, const GsCall& g, cudaStream_t
     // extended kernels only when the run uses MRAF / HIO, an illumination profile or a
     // multi-amplitude SLM
     const int x = (g.mix > 0.f || lit || p->levels < 0) ? 1 : 0;
-    const void* k_init = tiled ? c.rk->init_t[ti][x] : c.rk->init[x];
-    const void* k_row[2] = {tiled ? c.rk->gs_t[ti][0][x] : c.rk->gs[0][x],
-                            tiled ? c.rk->gs_t[ti][1][x] : c.rk->gs[1][x]};
-    const void* k_col[2] = {tiled ? c.ck->tiled[ti].gs[0][x] : c.ck->gs[0][x],
-                            tiled ? c.ck->tiled[ti].gs[1][x] : c.ck->gs[1][x]};
+    // the alternative radix plan per pass, where chosen and compiled for this width (plain runs)
+    const bool prow = tiled && x == 0 && c.pv_row == 1 && c.rk->init_tp[ti] != nullptr;
+    const bool pcol = tiled && x == 0 && c.pv_col == 1 && c.ck->tiled[ti].gs_p[0] != nullptr;
+    const void* k_init = prow ? c.rk->init_tp[ti] : (tiled ? c.rk->init_t[ti][x] : c.rk->init[x]);
+    const void* k_row[2] = {prow ? c.rk->gs_tp[ti][0] : (tiled ? c.rk->gs_t[ti][0][x] : c.rk->gs[0][x]),
+                            prow ? c.rk->gs_tp[ti][1] : (tiled ? c.rk->gs_t[ti][1][x] : c.rk->gs[1][x])};
+    const void* k_col[2] = {pcol ? c.ck->tiled[ti].gs_p[0] : (tiled ? c.ck->tiled[ti].gs[0][x] : c.ck->gs[0][x]),
+                            pcol ? c.ck->tiled[ti].gs_p[1] : (tiled ? c.ck->tiled[ti].gs[1][x] : c.ck->gs[1][x])};
     const int rrows = tiled ? c.rk->rows_t[ti] : c.rk->rows;
-    const int rnt = tiled ? c.rk->nt_t[ti] : c.rk->nt;
-    const int rsm = tiled ? c.rk->smem_t[ti] : c.rk->smem;
-    const int cnt = tiled ? c.ck->tiled[ti].nt : c.ck->nt;
-    const int csm = tiled ? c.ck->tiled[ti].smem_gs : c.ck->smem_gs;
+    const int rnt = prow ? c.rk->nt_tp[ti] : (tiled ? c.rk->nt_t[ti] : c.rk->nt);
+    const int rsm = prow ? c.rk->smem_tp[ti] : (tiled ? c.rk->smem_t[ti] : c.rk->smem);
+    const int cnt = pcol ? c.ck->tiled[ti].nt_p : (tiled ? c.ck->tiled[ti].nt : c.ck->nt);
+    const int csm = pcol ? c.ck->tiled[ti].smem_gs_p : (tiled ? c.ck->tiled[ti].smem_gs : c.ck->smem_gs);
+    if (prow) a.tw_row = p->tw_alt.at(c.W);
+    if (pcol) a.tw_col = p->tw_alt.at(c.H);
     const dim3 grow((c.H + rrows - 1) / rrows, nb), gcol(strips, nb);
     // prologue (writes h_0 out when there is no iteration)
     hg::PassArgs a0 = a;
@@ -1452,25 +1467,37 @@ hg_status hg_hio_run(hg_plan* p, const float* const* target_amp, const uint8_t* 
 
 // ---------------------------------------------------------------- autotuner
 //
-// For every size class of a single-plane plan, times a short GS run (6 iterations, seeded start, a
-// zero target in plan-owned scratch: the kernels' work does not depend on the values) with each
-// strip width the class allows -- 2 / 4 / 8 / 16 columns on the tiled field, or the row-major
-// field -- and keeps the fastest.  Choices are cached per process by (device, H, W, items in the
-// class, quantisation, propagation), so plans of the same shape reuse them.
+// For every size class of a single-plane plan, times a short GS run (10 iterations, seeded start, a
+// zero target in plan-owned scratch: the kernels' work does not depend on the values; the fastest of
+// five runs) with each strip width the class allows -- 2 / 4 / 8 / 16 columns on the tiled field,
+// the whole-run cluster kernel, or the row-major field -- and, on a tiled field, each radix plan of
+// the row and column passes, and keeps the fastest.  Choices are cached per process by (device, H,
+// W, items in the class, quantisation, propagation), so plans of the same shape reuse them.
 
 namespace {
 std::mutex g_tune_mu;
-std::map<std::vector<int64_t>, int> g_tune_cache;
+std::map<std::vector<int64_t>, std::array<int, 3>> g_tune_cache;  // (width, row plan, column plan)
 }  // namespace
 
 static hg_status autotune_class(hg_plan* p, SizeClass& c, cudaStream_t st) {
-  std::vector<int> cand;
-  if (c.tileable(-1, p->P)) cand.push_back(-1);  // whole run in one cluster per item
+  // candidates (width, row plan, column plan): the cluster kernel and the row-major field take the
+  // default plans; a tiled width also takes the alternative plan of either pass where compiled
+  struct Cand {
+    int w, pr, pc;
+  };
+  std::vector<Cand> cand;
+  if (c.tileable(-1, p->P)) cand.push_back({-1, 0, 0});  // whole run in one cluster per item
   for (int w : {2, 4, 8, 16})
-    if (c.tileable(w, p->P)) cand.push_back(w);
-  cand.push_back(0);  // row-major field
+    if (c.tileable(w, p->P)) {
+      const int ti = tile_index(w);
+      const bool ar = c.rk->init_tp[ti] != nullptr, ac = c.ck->tiled[ti].gs_p[0] != nullptr;
+      for (int pr = 0; pr <= (ar ? 1 : 0); ++pr)
+        for (int pc = 0; pc <= (ac ? 1 : 0); ++pc) cand.push_back({w, pr, pc});
+    }
+  cand.push_back({0, 0, 0});  // row-major field
   if (cand.size() == 1) {
     c.tile = 0;
+    c.pv_row = c.pv_col = 0;
     return HG_OK;
   }
   const std::vector<int64_t> key{p->device, c.H, c.W, (int64_t)c.items.size(), p->levels, p->propagation};
@@ -1478,7 +1505,9 @@ static hg_status autotune_class(hg_plan* p, SizeClass& c, cudaStream_t st) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune_cache.find(key);
     if (it != g_tune_cache.end()) {
-      c.tile = it->second;
+      c.tile = it->second[0];
+      c.pv_row = it->second[1];
+      c.pv_col = it->second[2];
       return HG_OK;
     }
   }
@@ -1490,38 +1519,50 @@ static hg_status autotune_class(hg_plan* p, SizeClass& c, cudaStream_t st) {
   } guard{zero};
   HG_CUDA(cudaMemsetAsync(zero, 0, (size_t)c.H * c.W * sizeof(float), st), "memset");
   std::vector<const float*> targets(p->n_items * p->P, zero);
-  const GsCall call{targets.data(), nullptr, 1, 6, nullptr, nullptr, nullptr};
+  const GsCall call{targets.data(), nullptr, 1, 10, nullptr, nullptr, nullptr};
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   HG_CUDA(cudaEventCreate(&e0), "event");
   HG_CUDA(cudaEventCreate(&e1), "event");
   float best_ms = 0.f;
-  int best = cand[0];
+  Cand best = cand[0];
   hg_status s = HG_OK;
-  for (int w : cand) {
-    c.tile = w;
+  for (const Cand& cd : cand) {
+    c.tile = cd.w;
+    c.pv_row = cd.pr;
+    c.pv_col = cd.pc;
     if ((s = gs_class(p, c, call, st)) != HG_OK) break;  // warm-up
-    cudaEventRecord(e0, st);
-    for (int r = 0; r < 3 && s == HG_OK; ++r) s = gs_class(p, c, call, st);
-    cudaEventRecord(e1, st);
-    if (s != HG_OK) break;
-    cudaError_t e = cudaEventSynchronize(e1);
+    // the fastest of five 10-iteration runs (one run of a small class takes tens of microseconds,
+    // so single timings are noisy; the minimum is the steadiest estimate)
     float ms = 0.f;
-    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    cudaError_t e = cudaSuccess;
+    for (int r = 0; r < 5 && s == HG_OK && e == cudaSuccess; ++r) {
+      cudaEventRecord(e0, st);
+      s = gs_class(p, c, call, st);
+      cudaEventRecord(e1, st);
+      if (s != HG_OK) break;
+      float one = 0.f;
+      e = cudaEventSynchronize(e1);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&one, e0, e1);
+      if (r == 0 || one < ms) ms = one;
+    }
+    if (s != HG_OK) break;
     if (e != cudaSuccess) {
       s = cuda_fail(e, "autotune timing");
       break;
     }
-    if (w == cand[0] || ms < best_ms) {
+    if (&cd == &cand[0] || ms < best_ms) {
       best_ms = ms;
-      best = w;
+      best = cd;
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  c.tile = best;
+  c.tile = best.w;
+  c.pv_row = best.pr;
+  c.pv_col = best.pc;
   if (s != HG_OK) return s;
   std::lock_guard<std::mutex> lk(g_tune_mu);
-  g_tune_cache[key] = best;
+  g_tune_cache[key] = {best.w, best.pr, best.pc};
   return HG_OK;
 }
 
@@ -1565,6 +1606,35 @@ hg_status hg_plan_strip_width(const hg_plan* p, int32_t item, int32_t* width_out
   if (item < 0 || item >= p->n_items) return fail(HG_ERR_INVALID_ARG, "item %d out of range", item);
   if (!width_out) return fail(HG_ERR_INVALID_ARG, "width_out is NULL");
   *width_out = p->classes[p->item_class[item]].tile;
+  return HG_OK;
+}
+
+hg_status hg_plan_set_radix_plan(hg_plan* p, int32_t item, int32_t row_plan, int32_t col_plan) {
+  if (!p) return fail(HG_ERR_INVALID_ARG, "plan is NULL");
+  if (item < 0 || item >= p->n_items) return fail(HG_ERR_INVALID_ARG, "item %d out of range", item);
+  SizeClass& c = p->classes[p->item_class[item]];
+  if (row_plan != 0 && row_plan != 1) return fail(HG_ERR_INVALID_ARG, "row_plan must be 0 or 1");
+  if (col_plan != 0 && col_plan != 1) return fail(HG_ERR_INVALID_ARG, "col_plan must be 0 or 1");
+  if (row_plan == 1 && !c.rk->has_alt)
+    return fail(HG_ERR_INVALID_ARG, "row length %d has no alternative radix plan", c.W);
+  if (col_plan == 1 && !c.ck->has_alt)
+    return fail(HG_ERR_INVALID_ARG, "column length %d has no alternative radix plan", c.H);
+  DeviceGuard g(p->device);
+  if (!g.ok) return fail(HG_ERR_CUDA, "cannot select device %d", p->device);
+  HG_CUDA(cudaDeviceSynchronize(), "device error");
+  c.pv_row = row_plan;
+  c.pv_col = col_plan;
+  for (auto& slot : p->gslot) p->drop_graph(slot);
+  return HG_OK;
+}
+
+hg_status hg_plan_radix_plan(const hg_plan* p, int32_t item, int32_t* row_plan, int32_t* col_plan) {
+  if (!p) return fail(HG_ERR_INVALID_ARG, "plan is NULL");
+  if (item < 0 || item >= p->n_items) return fail(HG_ERR_INVALID_ARG, "item %d out of range", item);
+  if (!row_plan || !col_plan) return fail(HG_ERR_INVALID_ARG, "output is NULL");
+  const SizeClass& c = p->classes[p->item_class[item]];
+  *row_plan = c.pv_row;
+  *col_plan = c.pv_col;
   return HG_OK;
 }
 

@@ -381,6 +381,32 @@ HG_PLAN(1536, 16, 16, 6)
 HG_PLAN(1920, 16, 8, 15)
 #undef HG_PLAN
 
+// A second radix plan for some lengths (the same three-stage split in another order, or another
+// split).  The order changes the stages' twiddle tables, exchange patterns and thread counts, and
+// which plan is faster differs between the row and the column pass (measured on GB300, 2048^2
+// GS: 16-8-16 rows 24.4 us against 25.1 with 16-16-8, columns 21.8 against 21.6), so the GS passes
+// are compiled with both and hg_plan_autotune picks per pass.  PlanV<N, 0> is the default plan.
+template <int N, int PV>
+struct PlanV {
+  using type = typename PlanFor<N>::type;
+};
+#define HG_ALT_PLAN(N, ...)          \
+  template <>                        \
+  struct PlanV<N, 1> {               \
+    using type = RList<__VA_ARGS__>; \
+  };
+HG_ALT_PLAN(864, 9, 6, 16)
+HG_ALT_PLAN(1024, 4, 16, 16)
+HG_ALT_PLAN(1080, 15, 9, 8)
+HG_ALT_PLAN(1536, 16, 6, 16)
+HG_ALT_PLAN(1920, 15, 8, 16)
+HG_ALT_PLAN(2048, 16, 8, 16)
+#undef HG_ALT_PLAN
+template <int N>
+__host__ __device__ constexpr bool has_alt_plan() {
+  return !std::is_same<typename PlanV<N, 1>::type, typename PlanFor<N>::type>::value;
+}
+
 // Values a thread holds in the widest stage of plan L when NT threads transform B sequences of
 // length N (each stage: ceil(B N / R / NT) butterflies of R values).
 template <class L>
@@ -412,20 +438,19 @@ template <int... Rs>
 struct RAll<RList<Rs...>> {
   __host__ __device__ static constexpr bool divisible(int n, int g) { return ((n / Rs % g == 0) && ...); }
 };
-template <int N, int G>
+template <int N, int G, int PV = 0>
 __host__ __device__ constexpr bool row_tileable() {
-  return G > 0 && N % 16 == 0 && N % G == 0 && RAll<typename PlanFor<N>::type>::divisible(N, G);
+  return G > 0 && N % 16 == 0 && N % G == 0 && RAll<typename PlanV<N, PV>::type>::divisible(N, G);
 }
 
 // Per-stage twiddle tables of length N.  A stage of radix R after Ns earlier points needs
 // w_{Ns R}^{r k} for r = 1..R-1, k = 0..Ns-1; its table stores them r-major, entry (r-1) Ns + k, so a
 // warp whose lanes hold consecutive k reads consecutive entries.  The stages read only the r = 1
 // row and form the higher powers by multiplication (stage_compute).  The blob holds the tables of
-// every stage (Ns > 1) of the forward plan, then those of the reversed plan that are not already
+// every stage (Ns > 1) of the forward plan F, then those of the reversed plan that are not already
 // present.
-template <int N>
+template <int N, class F = typename PlanFor<N>::type>
 struct TwBlob {
-  using F = typename PlanFor<N>::type;
   using Bk = typename RRev<F>::type;
   static constexpr int S = RArr<F>::n;
   __host__ __device__ static constexpr int stage_r(int which, int s) {
@@ -584,7 +609,7 @@ __device__ __forceinline__ void for_each_slot_jr(int t, F&& f) {
   }
 }
 
-template <class G, int R, int NS, bool INV, int V>
+template <class G, int R, int NS, bool INV, class F, int V>
 __device__ __forceinline__ void stage_compute(float2 (&v)[V], int t, const float2* __restrict__ tw) {
 #pragma unroll
   for (int i = 0; i < G::template bpt<R>(); ++i) {
@@ -592,7 +617,7 @@ __device__ __forceinline__ void stage_compute(float2 (&v)[V], int t, const float
     if (!G::template bf<R>(t, i, b, j)) continue;
     float2* x = &v[i * R];
     if constexpr (NS > 1) {
-      constexpr int off = TwBlob<G::N>::offset(NS, R);
+      constexpr int off = TwBlob<G::N, F>::offset(NS, R);
       static_assert(off >= 0, "missing twiddle table");
       // w^r for r >= 2 by repeated multiplication from the table's w = w_{Ns R}^{j mod Ns}: one load
       // per butterfly instead of R - 1 (the loads measured ~8 % of a GS iteration, the extra
@@ -663,20 +688,21 @@ __device__ __forceinline__ void stage_load(float2 (&v)[V], const float2* sm, int
 }
 
 // Run all stages of plan L (registers already hold the first stage's inputs); on return the
-// registers hold the last stage's outputs.  Uses sm as the exchange buffer (B*N float2).
-template <class G, bool INV, int NS, class L>
+// registers hold the last stage's outputs.  Uses sm as the exchange buffer (B*N float2).  F is the
+// forward plan of the pass (L is F or F reversed): it names the twiddle blob tw holds.
+template <class G, bool INV, int NS, class L, class F = typename PlanFor<G::N>::type>
 struct FftRun;
-template <class G, bool INV, int NS, int R, int... Rs>
-struct FftRun<G, INV, NS, RList<R, Rs...>> {
+template <class G, bool INV, int NS, int R, int... Rs, class F>
+struct FftRun<G, INV, NS, RList<R, Rs...>, F> {
   template <int V>
   __device__ __forceinline__ static void run(float2 (&v)[V], float2* sm, int t, const float2* __restrict__ tw) {
-    stage_compute<G, R, NS, INV>(v, t, tw);
+    stage_compute<G, R, NS, INV, F>(v, t, tw);
     if constexpr (sizeof...(Rs) > 0) {
       __syncthreads();  // everyone is done reading sm from the previous exchange
       stage_store<G, R, NS>(v, sm, t);
       __syncthreads();
       stage_load<G, RFirst<RList<Rs...>>::value, alt_exchange<R, NS>()>(v, sm, t);
-      FftRun<G, INV, NS * R, RList<Rs...>>::run(v, sm, t, tw);
+      FftRun<G, INV, NS * R, RList<Rs...>, F>::run(v, sm, t, tw);
     }
   }
 };

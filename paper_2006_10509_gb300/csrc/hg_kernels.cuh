@@ -48,14 +48,15 @@ __device__ __forceinline__ T* opaque(T* x) {
 // column-strip tiles of width TW (see fidx); the tile holds 16 / TW rows (2 for TW = 2) whose lanes
 // interleave in groups of TW, so each warp access covers whole 128-byte lines of the tiled layout
 // (whole 32-byte sectors for TW = 2, where 8-row tiles of 1024 threads measured slower).
-template <int W, int TW = 0>
+// PV: the radix plan (PlanV<W, PV>; 0 the default, 1 the alternative of the lengths that have one).
+template <int W, int TW = 0, int PV = 0>
 struct RowCfg {
   static constexpr int ROWS = TW ? (TW >= 4 ? 16 / TW : 2) : hg_max(1, 4096 / W);
   static constexpr int NT =
-      pick_threads<typename PlanFor<W>::type>(W, ROWS, value_budget(W), TW ? 1024 : 512);
+      pick_threads<typename PlanV<W, PV>::type>(W, ROWS, value_budget(W), TW ? 1024 : 512);
   static constexpr int MINB = hg_min(8, hg_max(1, 1024 / NT));  // CTAs per SM at <= 64 registers
   using G = Geo<W, ROWS, NT, false, (TW && ROWS > 1) ? TW : 0>;
-  using Fwd = typename PlanFor<W>::type;
+  using Fwd = typename PlanV<W, PV>::type;
   using Inv = typename RRev<Fwd>::type;
   static constexpr int RE = RLast<Fwd>::value;   // radix of the global load/store stages
   static constexpr int RM = RFirst<Fwd>::value;  // radix of the pointwise step between the FFTs
@@ -81,12 +82,12 @@ __host__ __device__ constexpr int natural_cols(int h) {
 // Column strip: C columns of length H, about 16 values per thread.  CW = 0: the row-major-field
 // width; CW > 0: a strip of the tiled GS field of that width (the plan's default is tiled_cols(H),
 // the autotuner may pick another).
-template <int H, int CW = 0>
+template <int H, int CW = 0, int PV = 0>
 struct ColCfg {
   static constexpr int C = CW ? CW : natural_cols(H);
-  static constexpr int NT = pick_threads<typename PlanFor<H>::type>(H, C, value_budget(H), 1024);
+  static constexpr int NT = pick_threads<typename PlanV<H, PV>::type>(H, C, value_budget(H), 1024);
   using G = Geo<H, C, NT, true>;
-  using Fwd = typename PlanFor<H>::type;
+  using Fwd = typename PlanV<H, PV>::type;
   using Inv = typename RRev<Fwd>::type;
   static constexpr int RB = RFirst<Fwd>::value;  // radix of the global load/store stage
   static constexpr int V = MaxV<G, Fwd>::value;
@@ -127,15 +128,19 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 template <int H, int C, int NT>
 __device__ __forceinline__ void prefetch_strip(float* ts, const float* __restrict__ A, int col0, int W) {
   const int t = threadIdx.x;
-  const bool vec = (C % 4 == 0) && (W % 4 == 0) && (col0 + C <= W) && (((uintptr_t)A & 15) == 0) &&
-                   ((__cvta_generic_to_shared(ts) & 15) == 0);
-  if (vec) {
-    constexpr int CH = C / 4;  // 16-byte chunks per row
-    for (int i = t; i < H * CH; i += NT) {
-      const int n = i / CH, c = i % CH;
-      cp_async16(ts + n * C + 4 * c, A + (size_t)n * W + col0 + 4 * c);
+  bool vec = false;
+  if constexpr (C % 4 == 0) {
+    vec = (W % 4 == 0) && (col0 + C <= W) && (((uintptr_t)A & 15) == 0) &&
+          ((__cvta_generic_to_shared(ts) & 15) == 0);
+    if (vec) {
+      constexpr int CH = C / 4;  // 16-byte chunks per row
+      for (int i = t; i < H * CH; i += NT) {
+        const int n = i / CH, c = i % CH;
+        cp_async16(ts + n * C + 4 * c, A + (size_t)n * W + col0 + 4 * c);
+      }
     }
-  } else {
+  }
+  if (!vec) {
     for (int i = t; i < H * C; i += NT) {
       const int n = i / C, b = i % C;
       if (col0 + b < W)
@@ -513,9 +518,9 @@ __device__ __forceinline__ void store_row_slots(const float2 (&v)[K::V], float2*
 
 // GS prologue: h0 = P_SLM(exp(i phi0)) (phi0 given, or drawn from the seed), times the chirp,
 // forward row FFTs -> field.  h0 is written out when phase_out / level_out are set.
-template <int W, int TW, bool EXT = false>
-__global__ void __launch_bounds__(RowCfg<W, TW>::NT, RowCfg<W, TW>::MINB) k_row_init(const __grid_constant__ PassArgs a) {
-  using K = RowCfg<W, TW>;
+template <int W, int TW, bool EXT = false, int PV = 0>
+__global__ void __launch_bounds__(RowCfg<W, TW, PV>::NT, RowCfg<W, TW, PV>::MINB) k_row_init(const __grid_constant__ PassArgs a) {
+  using K = RowCfg<W, TW, PV>;
   using G = typename K::G;
   extern __shared__ __align__(16) float2 sm[];
   const int t = threadIdx.x, k = blockIdx.y;
@@ -548,15 +553,15 @@ __global__ void __launch_bounds__(RowCfg<W, TW>::NT, RowCfg<W, TW>::MINB) k_row_
     }
     v[s] = h;
   });
-  FftRun<G, false, 1, typename K::Fwd>::run(v, sm, t, a.tw_row);
+  FftRun<G, false, 1, typename K::Fwd, typename K::Fwd>::run(v, sm, t, a.tw_row);
   store_row_slots<K, RLast<typename K::Fwd>::value, TW>(v, f, t, row0, H);
 }
 
 // GS row pass: inverse row FFTs, conj chirp, SLM projection (optionally written out), chirp,
 // forward row FFTs.
-template <int W, bool OUT, int TW, bool EXT = false>
-__global__ void __launch_bounds__(RowCfg<W, TW>::NT, RowCfg<W, TW>::MINB) k_row_gs(const __grid_constant__ PassArgs a) {
-  using K = RowCfg<W, TW>;
+template <int W, bool OUT, int TW, bool EXT = false, int PV = 0>
+__global__ void __launch_bounds__(RowCfg<W, TW, PV>::NT, RowCfg<W, TW, PV>::MINB) k_row_gs(const __grid_constant__ PassArgs a) {
+  using K = RowCfg<W, TW, PV>;
   using G = typename K::G;
   extern __shared__ __align__(16) float2 sm[];
   const int t = threadIdx.x, k = blockIdx.y;
@@ -567,7 +572,7 @@ __global__ void __launch_bounds__(RowCfg<W, TW>::NT, RowCfg<W, TW>::MINB) k_row_
   float2* f = a.field + (size_t)a.class_slot[k] * H * W;
   float2 v[K::V];
   load_row_slots<K, K::RE, TW>(v, f, t, row0, H);
-  FftRun<G, true, 1, typename K::Inv>::run(v, sm, t, a.tw_row);
+  FftRun<G, true, 1, typename K::Inv, typename K::Fwd>::run(v, sm, t, a.tw_row);
   float* po = OUT ? a.phase_out[k] : nullptr;
   uint8_t* lo = OUT ? a.level_out[k] : nullptr;
   // a multi-amplitude SLM's projection depends on the scale of g: bring the unnormalised field to
@@ -605,7 +610,7 @@ __global__ void __launch_bounds__(RowCfg<W, TW>::NT, RowCfg<W, TW>::MINB) k_row_
     pointwise(std::true_type{});
   else
     pointwise(std::false_type{});
-  FftRun<G, false, 1, typename K::Fwd>::run(v, sm, t, a.tw_row);
+  FftRun<G, false, 1, typename K::Fwd, typename K::Fwd>::run(v, sm, t, a.tw_row);
   // tiled: re-derive the (run-time stride) store addresses rather than keep the load's live
   if (TW)
     store_row_slots<K, K::RE, TW>(v, opaque(f), t, row0, opaque(H));
@@ -672,11 +677,11 @@ __device__ __forceinline__ size_t target_index(const PassArgs& a, int n, int col
 // also take the signal / noise regions of MRAF and HIO (the plain ones stay free of the per-pixel
 // test).  HIO keeps its noise-region input X between passes: on the signal region X' = A_s Y / |Y|
 // is the replacement itself, so X is stored for the noise region only.
-template <int H, bool REPLACE, int CT, bool EXT = false>
-__global__ void __launch_bounds__(ColCfg<H, CT>::NT, ColCfg<H, CT>::MINB)
+template <int H, bool REPLACE, int CT, bool EXT = false, int PV = 0>
+__global__ void __launch_bounds__(ColCfg<H, CT, PV>::NT, ColCfg<H, CT, PV>::MINB)
     k_col_gs(const __grid_constant__ PassArgs a) {
   constexpr bool TILED = CT > 0;
-  using K = ColCfg<H, CT>;
+  using K = ColCfg<H, CT, PV>;
   using G = typename K::G;
   extern __shared__ __align__(16) float2 sm[];
   const int P = a.n_planes > 1 ? a.n_planes : 1;
@@ -710,7 +715,7 @@ __global__ void __launch_bounds__(ColCfg<H, CT>::NT, ColCfg<H, CT>::MINB)
     else
       v[s] = col < W ? f[n * W + col] : make_float2(0.f, 0.f);  // 32-bit offsets: H W < 2^31
   });
-  FftRun<G, false, 1, typename K::Fwd>::run(v, sm, t, a.tw_col);
+  FftRun<G, false, 1, typename K::Fwd, typename K::Fwd>::run(v, sm, t, a.tw_col);
   cp_async_wait_all();
   __syncthreads();
   float s_it = 0.f, s_ii = 0.f, s_tt = 0.f;
@@ -742,7 +747,7 @@ __global__ void __launch_bounds__(ColCfg<H, CT>::NT, ColCfg<H, CT>::MINB)
     }
   });
   if (REPLACE) {
-    FftRun<G, true, 1, typename K::Inv>::run(v, sm, t, a.tw_col);
+    FftRun<G, true, 1, typename K::Inv, typename K::Fwd>::run(v, sm, t, a.tw_col);
     if (TILED) {
       float2* fo = opaque(fs);
       for_each_slot<G, K::RB>(t, [&](int s, int b, int n) { fo[n * K::C + b] = v[s]; });

@@ -42,6 +42,14 @@ struct RowKernels {
   const void* init_t[4][2];
   const void* gs_t[4][2][2];
   int rows_t[4], nt_t[4], smem_t[4];
+  // the plain tiled GS row kernels with the length's alternative radix plan (has_alt; nullptr
+  // otherwise or where that plan does not tile): prologue, pass with OUT = false / true; threads and
+  // shared memory of those tiles (the rows are rows_t)
+  int has_alt;
+  const void* init_tp[4];
+  const void* gs_tp[4][2];
+  int nt_tp[4], smem_tp[4];
+  TwiddleLayout tw_alt;     // twiddle tables of the alternative plan
   const void* fft[2][2];    // k_row_fft<INV><PRE>
   const void* ospr[2];      // k_row_ospr<BITS = false / true>
   int smem_ospr;            // dynamic shared memory of k_row_ospr (field tile + bit decisions)
@@ -79,7 +87,13 @@ struct ColKernels {
   struct Tiled {
     int nt, smem_gs;
     const void* gs[2][2];
+    // the plain kernel with the alternative radix plan (REPLACE = false / true), its threads and
+    // shared memory; nullptr where the length has none or it does not fit
+    const void* gs_p[2];
+    int nt_p, smem_gs_p;
   } tiled[4];
+  int has_alt;
+  TwiddleLayout tw_alt;     // twiddle tables of the alternative plan
   int tile;
   const void* fft[2][2];    // k_col_fft<INV><POST>
   const void* ospr[3];      // k_col_ospr: [0] start only, [1] finish + start, [2] finish only

@@ -15,9 +15,9 @@ void allow_smem(F* f, int bytes) {
   if (bytes > 48 * 1024) cudaFuncSetAttribute((const void*)f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
-template <int N>
+template <int N, class F = typename PlanFor<N>::type>
 TwiddleLayout make_tw() {
-  using T = TwBlob<N>;
+  using T = TwBlob<N, F>;
   static_assert(T::count() <= 16, "too many twiddle tables");
   TwiddleLayout l{};
   l.size = T::size;
@@ -43,6 +43,28 @@ void fill_tiled(RowKernels& r, int i) {
     r.rows_t[i] = K::ROWS;
     r.nt_t[i] = K::NT;
     r.smem_t[i] = K::SMEM;
+  }
+}
+
+// the alternative radix plan's plain tiled GS row kernels
+template <int N, int TW>
+void fill_tiled_alt(RowKernels& r, int i) {
+  if constexpr (has_alt_plan<N>() && row_tileable<N, TW, 1>()) {
+    using K = RowCfg<N, TW, 1>;
+    r.init_tp[i] = (const void*)&k_row_init<N, TW, false, 1>;
+    r.gs_tp[i][0] = (const void*)&k_row_gs<N, false, TW, false, 1>;
+    r.gs_tp[i][1] = (const void*)&k_row_gs<N, true, TW, false, 1>;
+    r.nt_tp[i] = K::NT;
+    r.smem_tp[i] = K::SMEM;
+  }
+}
+
+template <int N, int TW>
+void set_tiled_alt_attrs() {
+  if constexpr (has_alt_plan<N>() && row_tileable<N, TW, 1>()) {
+    allow_smem(&k_row_init<N, TW, false, 1>, RowCfg<N, TW, 1>::SMEM);
+    allow_smem(&k_row_gs<N, false, TW, false, 1>, RowCfg<N, TW, 1>::SMEM);
+    allow_smem(&k_row_gs<N, true, TW, false, 1>, RowCfg<N, TW, 1>::SMEM);
   }
 }
 
@@ -96,6 +118,11 @@ RowKernels make_row() {
   fill_tiled<N, 4>(r, 1);
   fill_tiled<N, 8>(r, 2);
   fill_tiled<N, 16>(r, 3);
+  r.has_alt = has_alt_plan<N>() ? 1 : 0;
+  fill_tiled_alt<N, 2>(r, 0);
+  fill_tiled_alt<N, 4>(r, 1);
+  fill_tiled_alt<N, 8>(r, 2);
+  fill_tiled_alt<N, 16>(r, 3);
   r.fft[0][0] = (const void*)&k_row_fft<N, false, false>;
   r.fft[0][1] = (const void*)&k_row_fft<N, false, true>;
   r.fft[1][0] = (const void*)&k_row_fft<N, true, false>;
@@ -111,6 +138,7 @@ RowKernels make_row() {
   fill_cluster<N, 8>(r, 0);
   fill_cluster<N, 16>(r, 1);
   r.tw = make_tw<N>();
+  r.tw_alt = make_tw<N, typename PlanV<N, 1>::type>();
   return r;
 }
 
@@ -125,6 +153,13 @@ void fill_col_tiled(ColKernels::Tiled& t) {
     t.gs[1][0] = (const void*)&k_col_gs<N, true, C, false>;
     t.gs[1][1] = (const void*)&k_col_gs<N, true, C, true>;
   }
+  using KP = ColCfg<N, C, 1>;
+  if constexpr (has_alt_plan<N>() && K::FEASIBLE && KP::FEASIBLE) {
+    t.nt_p = KP::NT;
+    t.smem_gs_p = KP::SMEM_T;
+    t.gs_p[0] = (const void*)&k_col_gs<N, false, C, false, 1>;
+    t.gs_p[1] = (const void*)&k_col_gs<N, true, C, false, 1>;
+  }
 }
 
 template <int N, int C>
@@ -135,6 +170,11 @@ void set_col_tiled_attrs() {
     allow_smem(&k_col_gs<N, true, C, false>, K::SMEM_T);
     allow_smem(&k_col_gs<N, false, C, true>, K::SMEM_T);
     allow_smem(&k_col_gs<N, true, C, true>, K::SMEM_T);
+  }
+  using KP = ColCfg<N, C, 1>;
+  if constexpr (has_alt_plan<N>() && K::FEASIBLE && KP::FEASIBLE) {
+    allow_smem(&k_col_gs<N, false, C, false, 1>, KP::SMEM_T);
+    allow_smem(&k_col_gs<N, true, C, false, 1>, KP::SMEM_T);
   }
 }
 
@@ -155,6 +195,8 @@ ColKernels make_col() {
   fill_col_tiled<N, 8>(c.tiled[2]);
   fill_col_tiled<N, 16>(c.tiled[3]);
   c.tile = tiled_cols(N);
+  c.has_alt = has_alt_plan<N>() ? 1 : 0;
+  c.tw_alt = make_tw<N, typename PlanV<N, 1>::type>();
   c.fft[0][0] = (const void*)&k_col_fft<N, false, false>;
   c.fft[0][1] = (const void*)&k_col_fft<N, false, true>;
   c.fft[1][0] = (const void*)&k_col_fft<N, true, false>;
@@ -179,6 +221,10 @@ void set_row_attrs(const RowKernels& r) {
   set_tiled_attrs<HG_LEN, 4>();
   set_tiled_attrs<HG_LEN, 8>();
   set_tiled_attrs<HG_LEN, 16>();
+  set_tiled_alt_attrs<HG_LEN, 2>();
+  set_tiled_alt_attrs<HG_LEN, 4>();
+  set_tiled_alt_attrs<HG_LEN, 8>();
+  set_tiled_alt_attrs<HG_LEN, 16>();
   allow_smem(&k_row_fft<HG_LEN, false, false>, r.smem);
   allow_smem(&k_row_fft<HG_LEN, false, true>, r.smem);
   allow_smem(&k_row_fft<HG_LEN, true, false>, r.smem);

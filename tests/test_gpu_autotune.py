@@ -106,3 +106,63 @@ def test_strip_width_rejected_for_multiplane_plans():
             plan.set_strip_width(0, 2)
         plan.autotune()
         assert plan.strip_width(0) == 0
+
+
+# ------------------------------------------------------------------ radix plans
+
+PLAN_SIZES = [(2048, 2048, 0), (2048, 2048, 4), (1024, 1024, 8), (1080, 1920, 2), (864, 1536, 4)]
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("h, w, levels", PLAN_SIZES)
+def test_every_radix_plan_matches_the_oracle_one_step(h, w, levels):
+    """Each (row plan, column plan) of a length pair with alternatives: one teacher-forced GS step
+    against the FP64 oracle, and the NMSE of the start."""
+    from oracle import gs as ogs
+    from oracle import project
+    from oracle.fft import fft2
+    from oracle.metrics import nmse
+    from tests.helpers import check_continuous_phase, check_levels, check_nmse
+
+    import paper_2006_10509_gb300 as hg
+
+    dev = cuda_device()
+    a = synth.blur_target(h, w, 2.0, seed=500 + levels)
+    if levels:
+        phi0 = (2 * np.pi * np.random.default_rng(501).integers(0, levels, (h, w)) / levels).astype(np.float32)
+    else:
+        phi0 = synth.uniform_phase(h, w, seed=502)
+    a64 = a.astype(np.float64)
+    h0, _ = project.slm_project(np.exp(1j * phi0.astype(np.float64)), levels)
+    st = ogs.gs_step(h0, a64, levels)
+    e0 = nmse(np.abs(fft2(h0)) ** 2, a64 * a64)
+    with hg.Plan([h], [w], quant_levels=levels) as plan:
+        assert plan.strip_width(0) > 0  # the default tiled field
+        for pr in (0, 1):
+            for pc in (0, 1):
+                plan.set_radix_plan(0, pr, pc)
+                assert plan.radix_plan(0) == (pr, pc)
+                ph, lv, nm = _run(hg, dev, plan, a, phi0, 1, levels)
+                if levels:
+                    check_levels(lv, st["q"], st["g"], levels)
+                else:
+                    check_continuous_phase(ph, st["g"], st["h"])
+                check_nmse(nm[:1], [e0], rtol=1e-3)
+
+
+@pytest.mark.gpu
+def test_radix_plan_choice_errors_and_autotune():
+    import paper_2006_10509_gb300 as hg
+
+    cuda_device()
+    with hg.Plan([512, 2048], [512, 2048]) as plan:
+        with pytest.raises(hg.HologenError) as e:
+            plan.set_radix_plan(0, 1, 0)  # 512 has no alternative plan
+        assert e.value.status == hg.HG_ERR_INVALID_ARG
+        with pytest.raises(hg.HologenError) as e:
+            plan.set_radix_plan(1, 2, 0)
+        assert e.value.status == hg.HG_ERR_INVALID_ARG
+        assert plan.radix_plan(1) == (0, 0)
+        plan.autotune()
+        assert plan.radix_plan(0) == (0, 0)
+        assert plan.radix_plan(1)[0] in (0, 1) and plan.radix_plan(1)[1] in (0, 1)
