@@ -170,3 +170,32 @@ def test_gs_is_deterministic():
     r2 = _run(hg, dev, a, 5, 4, None, seed=3)
     assert np.array_equal(r1[1], r2[1]) and np.array_equal(r1[2], r2[2])
 
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("tuned", [False, True])
+def test_gs_2048_headline_curve_against_stored_oracle_curve(tuned):
+    """The headline run (2048^2, continuous, 100 iterations, target seed 0, start seed 1): the NMSE of
+    every iterate within 1 % of the FP64 oracle's curve in tests/golden/gs2048_curve.txt (written by
+    tests/golden/make_gs2048_curve.py, which also measured the oracle's self-sensitivity there: at
+    most 3e-7 relative over three 1e-7-rad start perturbations, so the curve is binding), with the
+    default kernels and with the autotuner's strip width and radix plans."""
+    import os
+
+    import paper_2006_10509_gb300 as hg
+
+    dev = cuda_device()
+    path = os.path.join(os.path.dirname(__file__), "golden", "gs2048_curve.txt")
+    ref = np.loadtxt(path)
+    assert ref.shape == (101, 3) and ref[:, 2].max() < 1e-3
+    import torch
+
+    a = synth.blur_target(2048, 2048, 2.0, seed=0)
+    phi0 = synth.uniform_phase(2048, 2048, seed=1)
+    with hg.Plan([2048], [2048]) as plan:
+        if tuned:
+            plan.autotune()
+        nm = torch.zeros((1, 101), dtype=torch.float32, device=dev)
+        plan.gs([torch.from_numpy(a).to(dev)], 100, init_phase=[torch.from_numpy(phi0).to(dev)], nmse_out=nm)
+        plan.sync()
+    check_nmse(nm.cpu().numpy()[0], ref[:, 1])
