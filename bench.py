@@ -23,8 +23,9 @@ Also reported:
   secondary     the rest of the metric, each timed over graph replays after warm-up and given
                 with its fraction of the HBM peak: the 4-level variant of the headline, GS at
                 4096^2 (the size whose working set leaves L2), OSPR 1080x1920 (16 targets x 24
-                subframes), and gradient descent vs multi-plane GS at 2048^2 with 3 Fresnel planes
-                (time to NMSE)
+                subframes), GS 256^2 and Fresnel GS 1024^2 8-level, gradient descent vs
+                multi-plane GS at 2048^2 with 3 Fresnel planes (time to NMSE), and the 64-hologram
+                mixed-size batch (holograms/s, p50 / p99 latency)
 
 --impl reference times the oracle (the only reference this method has) on the same workload.
 """
@@ -307,6 +308,14 @@ def run_ours(args):
     # graph mode: each step replays one CUDA graph of the run's 200+ launches (captured in the
     # warm-up); the last warm-up step also captures the timed variant of the graph
     plan = hg.Plan([H], [W])
+    if args.tuning:  # fixed choice (reproduces a tuned run without the autotuner's launches)
+        w_, pr_, pc_ = (int(x) for x in args.tuning.split(","))
+        plan.set_strip_width(0, w_)
+        plan.set_radix_plan(0, pr_, pc_)
+    else:
+        plan.autotune()  # strip width and per-pass radix plans (library autotuner)
+    tuned = {"strip_width": plan.strip_width(0), "radix_plan_row_col": list(plan.radix_plan(0)),
+             "by": "given" if args.tuning else "hg_plan_autotune"}
     plan.set_graph(True)
     for i in range(args.warmup):
         plan.set_timing(i == args.warmup - 1)
@@ -413,8 +422,12 @@ def run_ours(args):
         secondary = {}
         for w in ("gs2048q4", "gs4096", "ospr"):
             secondary[w] = time_workload(w, dev, 3, 10, tune=False)
+        for w in ("gs256", "fresnel1024"):  # configurations 1 and 2, strip widths autotuned
+            secondary[w] = time_workload(w, dev, 3, 10)
         g = gd_vs_gs(dev, 3)
         secondary["gd_vs_gs"] = {k: g[k] for k in ("workload", "metric", "time_to", "gd", "gs")}
+        b = batch_workload(dev, 3, 5)
+        secondary["batch"] = {k: v for k, v in b.items() if k not in ("by_size_last_run",)}
         torch.cuda.synchronize()
     cpu = None
     if ws == 1 and not args.no_cpu_baseline:
@@ -431,7 +444,7 @@ def run_ours(args):
         "config": {"workload": WORKLOAD, "H": H, "W": W, "n_iter": N_ITER, "quant_levels": 0,
                    "target": f"smoothed noise sigma {SIGMA} px, seed 0+rank", "init_phase": "uniform, seed 1+rank",
                    "l2": "flushed (512 MiB write) before every timed step", "parallelism": f"replicas x{ws}",
-                   "launch": "CUDA graph replay per step (library graph mode)",
+                   "launch": "CUDA graph replay per step (library graph mode)", "autotuned": tuned,
                    "kernel_times": "shares from event nodes of a timed graph copy replayed after the timed "
                                    "region, times the untimed step time",
                    "final_nmse": final_nmse},
@@ -445,6 +458,16 @@ def run_ours(args):
 
 
 def run_batch(args):
+    """Prints batch_workload (below) as one JSON line."""
+    import torch
+
+    from __graft_entry__ import build
+
+    build()
+    print(json.dumps(batch_workload(torch.device("cuda", 0), args.warmup, args.steps)))
+
+
+def batch_workload(dev, warmup: int, steps: int) -> dict:
     """Mixed-size serving batch: 64 Fourier GS holograms, sizes drawn with seed 5000 from
     {512^2, 1024^2, 1536x864, 2048^2, 4096^2}, smoothed-noise targets (seeds 5001..5064), 4-level
     phase, 50 iterations, starting phase drawn on the device; strip widths autotuned per size class;
@@ -456,10 +479,7 @@ def run_batch(args):
 
     import paper_2006_10509_gb300 as hg
     import synth
-    from __graft_entry__ import build
 
-    build()
-    dev = torch.device("cuda", 0)
     sizes = synth.mixed_sizes(64, 5000)
     n_iter, levels = 50, 4
     targets = [torch.from_numpy(synth.blur_target(h, w, SIGMA, seed=5001 + i)).to(dev) for i, (h, w) in enumerate(sizes)]
@@ -474,11 +494,11 @@ def run_batch(args):
     phases = [torch.empty((h, w), dtype=torch.float32, device=dev) for h, w in sizes]
     plan.gs(targets, 0, seed=5000, phase_out=phases)
     plan.set_graph(True)
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         plan.gs(targets, n_iter, init_phase=phases, nmse_out=nm)
     torch.cuda.synchronize()
     lats, times = [], []
-    for _ in range(args.steps):
+    for _ in range(steps):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         plan.gs(targets, n_iter, init_phase=phases, nmse_out=nm)
@@ -520,10 +540,10 @@ def run_batch(args):
             "sequential_loop_ms": seq_ms, "speedup_vs_loop": seq_ms / ms,
             "final_nmse_median": float(np.median(final_batch)),
             "loop_same_final_nmse": bool(np.array_equal(final_batch, final_loop)),
-            "steps": args.steps, "warmup": args.warmup,
+            "steps": steps, "warmup": warmup,
             "sizes": {f"{h}x{w}": sum(1 for s in sizes if s == (h, w)) for h, w in sorted(set(sizes))},
             "autotuned_strip_widths": {f"{h}x{w}": widths[(h, w)] for h, w in sorted(set(sizes))}}
-    print(json.dumps(line))
+    return line
 
 
 CONFIG_WORKLOADS = ("gs256", "fresnel1024", "ospr", "mraf2048", "hio2048", "dbs128", "gs2048q4", "gs4096")
@@ -758,6 +778,8 @@ def main():
     ap.add_argument("--cpu-iters", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-secondary", action="store_true", help="skip the 'secondary' workloads of the headline line")
+    ap.add_argument("--tuning", default=None, metavar="W,ROWPLAN,COLPLAN",
+                    help="headline: use this strip width and these radix plans instead of the autotuner's")
     ap.add_argument("--workload", default="gs2048", choices=["gs2048", "batch", "gd", *CONFIG_WORKLOADS],
                     help="gs2048: the headline line; batch: the mixed-size serving batch; "
                          "gd: gradient descent vs multi-plane GS, time to NMSE; gs256 / fresnel1024 / ospr: "
