@@ -489,6 +489,7 @@ def batch_workload(dev, warmup: int, steps: int) -> dict:
     # strip widths of the tiled field per size class, picked by the library's autotuner
     plan.autotune()
     widths = {sizes[i]: plan.strip_width(i) for i in range(len(sizes))}
+    radix = {sizes[i]: plan.radix_plan(i) for i in range(len(sizes))}
     # starting phases: the device draw (seed 5000) projected to the levels, taken once so that the
     # per-hologram loop below starts every hologram from exactly the same field
     phases = [torch.empty((h, w), dtype=torch.float32, device=dev) for h, w in sizes]
@@ -507,11 +508,12 @@ def batch_workload(dev, warmup: int, steps: int) -> dict:
         times.append(e0.elapsed_time(e1))
     final_batch = nm[:, -1].cpu().numpy()
     plan.close()
-    # plain per-hologram loop: one-item plans, same kernels (same strip widths), launched one after
-    # another
+    # plain per-hologram loop: one-item plans, same kernels (same strip widths and radix plans),
+    # launched one after another
     singles = [hg.Plan([h], [w], quant_levels=levels) for h, w in sizes]
     for pl, sz in zip(singles, sizes):
         pl.set_strip_width(0, widths[sz])
+        pl.set_radix_plan(0, *radix[sz])
     nm1 = torch.zeros((64, n_iter + 1), dtype=torch.float32, device=dev)
     for k, pl in enumerate(singles):
         pl.gs([targets[k]], n_iter, init_phase=[phases[k]], nmse_out=nm1[k])
@@ -542,7 +544,8 @@ def batch_workload(dev, warmup: int, steps: int) -> dict:
             "loop_same_final_nmse": bool(np.array_equal(final_batch, final_loop)),
             "steps": steps, "warmup": warmup,
             "sizes": {f"{h}x{w}": sum(1 for s in sizes if s == (h, w)) for h, w in sorted(set(sizes))},
-            "autotuned_strip_widths": {f"{h}x{w}": widths[(h, w)] for h, w in sorted(set(sizes))}}
+            "autotuned_strip_widths": {f"{h}x{w}": widths[(h, w)] for h, w in sorted(set(sizes))},
+            "autotuned_radix_plans_row_col": {f"{h}x{w}": list(radix[(h, w)]) for h, w in sorted(set(sizes))}}
     return line
 
 
