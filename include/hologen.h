@@ -348,14 +348,15 @@ HG_API int64_t hg_plan_launch_count(const hg_plan* plan);
 HG_API hg_status hg_plan_set_graph(hg_plan* plan, int32_t enabled);
 
 /*
- * Autotuner (a tuning choice the plan owns; no counterpart in the paper).  Single-plane GS
- * keeps its field tiled in column strips so that a column pass reads its strip as one contiguous
- * block; the strip width trades the column pass's CTA size against the row pass's access pattern.
- * The plan starts from a measured default per column length.  hg_plan_autotune times, for every
- * size class, a 10-iteration GS run (seeded start, zero target in its own scratch; the fastest of
- * five runs) with each width
- * the class allows (2, 4, 8 or 16 columns, or a row-major field) and each radix plan of the row and
- * column passes (below) and keeps the fastest; choices are cached per process by (device, H, W,
+ * Autotuner (a tuning choice the plan owns; no counterpart in the paper).  GS keeps its field
+ * tiled in column strips so that a column pass reads its strip as one contiguous block; the strip
+ * width trades the column pass's CTA size against the row pass's access pattern.  The plan starts
+ * from a measured default per column length (multi-plane GS: that default where it is 2, 4 or 8
+ * columns, else a row-major field; gradient descent always keeps its field row-major).
+ * hg_plan_autotune times, for every size class, a 10-iteration GS run (seeded start, zero target
+ * in its own scratch; the fastest of five runs) with each width the class allows (2, 4, 8 or 16
+ * columns for one plane, 2, 4 or 8 for several, or a row-major field) and each radix plan of the
+ * row and column passes (below; single-plane only) and keeps the fastest; choices are cached per process by (device, H, W,
  * items in the class, levels, propagation).  It
  * synchronises `stream` before and after, allocates and frees one scratch target per class, does
  * not count or time its own launches, and drops captured graphs.  Results of later runs do not

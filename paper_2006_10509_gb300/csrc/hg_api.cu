@@ -145,7 +145,7 @@ struct SizeClass {
   const void* cl_fn = nullptr;
   int cl_nt = 0, cl_smem = 0;
   // whether the GS field can be tiled in strips of width w here (kernels exist, rows tile evenly);
-  // w = -1: the whole-run cluster kernel
+  // w = -1: the whole-run cluster kernel; several planes (multi-plane GS) take widths 2, 4 and 8
   bool tileable(int w, int planes) const;
 };
 
@@ -154,9 +154,10 @@ int tile_index(int cols) { return cols == 2 ? 0 : (cols == 4 ? 1 : (cols == 8 ? 
 
 bool SizeClass::tileable(int w, int planes) const {
   if (w == -1) return planes == 1 && cl > 0;
-  if (planes != 1 || (w != 2 && w != 4 && w != 8 && w != 16) || W % w != 0) return false;
+  if ((w != 2 && w != 4 && w != 8 && w != 16) || W % w != 0) return false;
   const int ti = tile_index(w);
-  return ck->tiled[ti].gs[0][0] != nullptr && rk->init_t[ti][0] != nullptr;
+  if (ck->tiled[ti].gs[0][0] == nullptr) return false;
+  return planes == 1 ? rk->init_t[ti][0] != nullptr : (rk->mp_init_t[ti] != nullptr && rk->mp_t[ti][0] != nullptr);
 }
 
 struct DeviceGuard {
@@ -917,7 +918,7 @@ hg_status gs_class(hg_plan* p, const SizeClass& c, const GsCall& g, cudaStream_t
     // (contiguous strips for the column pass), else row-major; MRAF, HIO and illuminated runs of a
     // class set to the cluster kernel take the default strip width
     const int width = c.tile == -1 ? (c.tileable(c.ck->tile, P) ? c.ck->tile : 0) : c.tile;
-    const bool tiled = P == 1 && width > 0;
+    const bool tiled = width > 0;
     const int ti = tiled ? tile_index(width) : 0;
     const int strip = tiled ? width : c.ck->cols;
     const int strips = tiled ? (c.W + width - 1) / width : c.col_blocks();
@@ -928,8 +929,16 @@ hg_status gs_class(hg_plan* p, const SizeClass& c, const GsCall& g, cudaStream_t
       return s;
     a.ttile = c.ttile;
     if (P > 1) {
-      // multi-plane GS: averaged projections over the P planes
-      const dim3 grow(c.row_blocks(), nb), gcol(c.col_blocks(), nb * P);
+      // multi-plane GS: averaged projections over the P planes, on the tiled field (strips of
+      // width C: the column passes stream contiguous strips) or the row-major one
+      const dim3 grow(tiled ? (c.H + c.rk->rows_t[ti] - 1) / c.rk->rows_t[ti] : c.row_blocks(), nb),
+          gcol(strips, nb * P);
+      const void* k_init = tiled ? c.rk->mp_init_t[ti] : c.rk->mp_init[1];
+      const void* k_row[2] = {tiled ? c.rk->mp_t[ti][0] : c.rk->mp[0], tiled ? c.rk->mp_t[ti][1] : c.rk->mp[1]};
+      const void* k_col[2] = {tiled ? c.ck->tiled[ti].gs[0][0] : c.ck->gs[0][0],
+                              tiled ? c.ck->tiled[ti].gs[1][0] : c.ck->gs[1][0]};
+      const int rnt = tiled ? c.rk->nt_t[ti] : c.rk->nt, rsm = tiled ? c.rk->smem_t[ti] : c.rk->smem;
+      const int cnt = tiled ? c.ck->tiled[ti].nt : c.ck->nt, csm = tiled ? c.ck->tiled[ti].smem_gs : c.ck->smem_gs;
       hg::PassArgs a0 = a, ao = a;
       for (int k = 0; k < nb; ++k) {
         const int item = c.items[c0 + k];
@@ -950,12 +959,12 @@ hg_status gs_class(hg_plan* p, const SizeClass& c, const GsCall& g, cudaStream_t
                 HG_OK ||
             (s = plane_forwards(p, c, K_ROW_MP_INIT, a, grow, st)) != HG_OK)
           return s;
-      } else if ((s = launch(p, K_ROW_MP_INIT, c.rk->mp_init[1], grow, c.rk->nt, c.rk->smem, a0, st)) != HG_OK) {
+      } else if ((s = launch(p, K_ROW_MP_INIT, k_init, grow, rnt, rsm, a0, st)) != HG_OK) {
         return s;
       }
       for (int it = 0; it < n_iter; ++it) {
         a.iter = it;
-        if ((s = launch(p, K_COL_GS, c.ck->gs[1][0], gcol, c.ck->nt, c.ck->smem_gs, a, st)) != HG_OK) return s;
+        if ((s = launch(p, K_COL_GS, k_col[1], gcol, cnt, csm, a, st)) != HG_OK) return s;
         const bool last = it == n_iter - 1;
         hg::PassArgs ar = last ? ao : a;
         ar.finalize = nmse_out != nullptr;
@@ -965,13 +974,13 @@ hg_status gs_class(hg_plan* p, const SizeClass& c, const GsCall& g, cudaStream_t
               (s = launch(p, K_ROW_MP, c.rk->plane.project, pointwise_grid(c, nb), 256, 0, ar, st, 0, acc)) != HG_OK ||
               (s = plane_forwards(p, c, K_ROW_MP, a, grow, st)) != HG_OK)
             return s;
-        } else if ((s = launch(p, K_ROW_MP, c.rk->mp[last], grow, c.rk->nt, c.rk->smem, ar, st)) != HG_OK) {
+        } else if ((s = launch(p, K_ROW_MP, k_row[last], grow, rnt, rsm, ar, st)) != HG_OK) {
           return s;
         }
       }
       a.iter = n_iter;
       a.fin_iter = n_iter;
-      if ((s = launch(p, K_COL_NMSE, c.ck->gs[0][0], gcol, c.ck->nt, c.ck->smem_gs, a, st)) != HG_OK) return s;
+      if ((s = launch(p, K_COL_NMSE, k_col[0], gcol, cnt, csm, a, st)) != HG_OK) return s;
       if (nmse_out && (s = launch(p, K_FINALIZE, (const void*)&hg::k_finalize<0>, gfin, 32, 0, a, st)) != HG_OK)
         return s;
       continue;
@@ -1490,7 +1499,8 @@ static hg_status autotune_class(hg_plan* p, SizeClass& c, cudaStream_t st) {
   for (int w : {2, 4, 8, 16})
     if (c.tileable(w, p->P)) {
       const int ti = tile_index(w);
-      const bool ar = c.rk->init_tp[ti] != nullptr, ac = c.ck->tiled[ti].gs_p[0] != nullptr;
+      // (the multi-plane kernels have the default plans only)
+      const bool ar = p->P == 1 && c.rk->init_tp[ti] != nullptr, ac = p->P == 1 && c.ck->tiled[ti].gs_p[0] != nullptr;
       for (int pr = 0; pr <= (ar ? 1 : 0); ++pr)
         for (int pc = 0; pc <= (ac ? 1 : 0); ++pc) cand.push_back({w, pr, pc});
     }

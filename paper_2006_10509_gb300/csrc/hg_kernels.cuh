@@ -286,7 +286,8 @@ __device__ __forceinline__ float2 slm_project(float2 g, int n_levels, const floa
   if (n_levels == 4) {
     // levels 0, pi/2, pi, 3pi/2: the sector of g from |x| against |y| and the signs, no arctangent
     // (measured on GB300: the 4-level GS row pass at 2048^2 29.8 -> 26.3 us).  A midpoint goes to
-    // the higher index: arg pi/4 -> 1, 3pi/4 -> 2, 5pi/4 -> 3, 7pi/4 -> 0.
+    // the higher index: arg pi/4 -> 1, 3pi/4 -> 2, 5pi/4 -> 3, 7pi/4 -> 0.  Other level counts use
+    // the arctangent below; 8 levels the quadrant folding that follows.
     const float ax = fabsf(g.x), ay = fabsf(g.y);
     int qq;
     if (ax > ay || (ax == ay && ((g.x > 0.f) != (g.y > 0.f))))
@@ -294,6 +295,28 @@ __device__ __forceinline__ float2 slm_project(float2 g, int n_levels, const floa
     else
       qq = g.y > 0.f ? 1 : 3;
     if (ax == 0.f && ay == 0.f) qq = 0;
+    q = qq;
+    return __ldg(&lev[qq]);
+  }
+  if (n_levels == 8) {
+    // levels k pi/4: fold g into the first quadrant (quarter turns Q, (u, v) with u > 0, v >= 0),
+    // then the sector from v against tan(pi/8) u and u against tan(pi/8) v (a midpoint to the
+    // higher index, as above; g = 0 -> 0)
+    constexpr float t8 = 0.41421356237309504880f;  // tan(pi/8) = sqrt(2) - 1
+    int qd;
+    float u, v;
+    if (g.x > 0.f && g.y >= 0.f) {
+      qd = 0, u = g.x, v = g.y;
+    } else if (g.x <= 0.f && g.y > 0.f) {
+      qd = 1, u = g.y, v = -g.x;
+    } else if (g.x < 0.f && g.y <= 0.f) {
+      qd = 2, u = -g.x, v = -g.y;
+    } else {
+      qd = 3, u = -g.y, v = g.x;
+    }
+    int qq = 2 * qd + (v < t8 * u ? 0 : (t8 * v >= u ? 2 : 1));
+    if (qq >= 8) qq -= 8;
+    if (g.x == 0.f && g.y == 0.f) qq = 0;
     q = qq;
     return __ldg(&lev[qq]);
   }
@@ -957,12 +980,13 @@ __device__ __forceinline__ float2 chirp_at(const PassArgs& a, int p, int n, int 
 
 // Start of a multi-plane run: h = P_SLM(exp(i phi)) (PROJECT; else h = exp(i phi) exactly, for
 // gradient descent), then for every plane p: forward row FFTs of h c_p -> field p.
-// GD reads phi from a.phi[k]; GS from a.phase_in[k] or the seed.
+// GD reads phi from a.phi[k]; GS from a.phase_in[k] or the seed.  TW > 0 (multi-plane GS): the
+// field tiled in column strips of width TW.
 // (Capped at 64 registers: measured on GB300, 2048^2 with 3 planes, 98 -> 73 us despite a few
 // spills; k_row_mp keeps its 128 registers, which measured faster than any cap.)
-template <int W, bool PROJECT>
-__global__ void __launch_bounds__(RowCfg<W>::NT, RowCfg<W>::MINB) k_row_mp_init(const __grid_constant__ PassArgs a) {
-  using K = RowCfg<W>;
+template <int W, bool PROJECT, int TW = 0>
+__global__ void __launch_bounds__(RowCfg<W, TW>::NT, RowCfg<W, TW>::MINB) k_row_mp_init(const __grid_constant__ PassArgs a) {
+  using K = RowCfg<W, TW>;
   using G = typename K::G;
   constexpr int R0 = RFirst<typename K::Fwd>::value;
   extern __shared__ __align__(16) float2 sm[];
@@ -1006,18 +1030,27 @@ __global__ void __launch_bounds__(RowCfg<W>::NT, RowCfg<W>::MINB) k_row_mp_init(
     });
     FftRun<G, false, 1, typename K::Fwd>::run(v, sm, t, a.tw_row);
     float2* f = a.field + ((size_t)slot * P + p) * H * W;
-    for_each_slot<G, RLast<typename K::Fwd>::value>(t, [&](int s, int b, int n) {
-      const int row = row0 + b;
-      if (row < H) f[(size_t)row * W + n] = v[s];
-    });
+    if constexpr (TW == 0) {
+      for_each_slot<G, RLast<typename K::Fwd>::value>(t, [&](int s, int b, int n) {
+        const int row = row0 + b;
+        if (row < H) f[(size_t)row * W + n] = v[s];
+      });
+    } else {
+      store_row_slots<K, RLast<typename K::Fwd>::value, TW>(v, f, t, row0, H);
+    }
   }
 }
 
 // Multi-plane GS row pass: for every plane inverse row FFTs and conj chirp, summed; SLM projection
 // of the sum (optionally written out); for every plane chirp and forward row FFTs.
-template <int W, bool OUT>
-__global__ void __launch_bounds__(RowCfg<W>::NT) k_row_mp(const __grid_constant__ PassArgs a) {
-  using K = RowCfg<W>;
+// TW > 0: the field tiled in column strips of width TW (as the tiled GS row pass reads it).
+// (Row-major instances have no minimum of CTAs per SM (0): ptxas then takes 128 registers at 2048,
+// measured faster than any cap, and an explicit minimum of 1 made it take 191 and the pass 30 %
+// longer.  Tiled instances are held to 2 CTAs of 256 threads per SM, which they would exceed.)
+template <int W, bool OUT, int TW = 0>
+__global__ void __launch_bounds__(RowCfg<W, TW>::NT, TW ? hg_max(1, 512 / RowCfg<W, TW>::NT) : 0)
+    k_row_mp(const __grid_constant__ PassArgs a) {
+  using K = RowCfg<W, TW>;
   using G = typename K::G;
   extern __shared__ __align__(16) float2 sm[];
   const int P = a.n_planes > 1 ? a.n_planes : 1;
@@ -1030,12 +1063,16 @@ __global__ void __launch_bounds__(RowCfg<W>::NT) k_row_mp(const __grid_constant_
 #pragma unroll
   for (int i = 0; i < K::V; ++i) g[i] = make_float2(0.f, 0.f);
   for (int p = 0; p < P; ++p) {
-    const float2* f = a.field + ((size_t)slot * P + p) * H * W;
     float2 v[K::V];
-    for_each_slot<G, K::RE>(t, [&](int s, int b, int n) {
-      const int row = row0 + b;
-      v[s] = row < H ? f[(size_t)row * W + n] : make_float2(0.f, 0.f);
-    });
+    const float2* f = a.field + ((size_t)slot * P + p) * H * W;
+    if constexpr (TW == 0) {
+      for_each_slot<G, K::RE>(t, [&](int s, int b, int n) {
+        const int row = row0 + b;
+        v[s] = row < H ? f[(size_t)row * W + n] : make_float2(0.f, 0.f);
+      });
+    } else {
+      load_row_slots<K, K::RE, TW>(v, f, t, row0, H);
+    }
     FftRun<G, true, 1, typename K::Inv>::run(v, sm, t, a.tw_row);
     for_each_slot<G, K::RM>(t, [&](int s, int b, int n) {
       const int row = row0 + b;
@@ -1064,10 +1101,14 @@ __global__ void __launch_bounds__(RowCfg<W>::NT) k_row_mp(const __grid_constant_
     });
     FftRun<G, false, 1, typename K::Fwd>::run(v, sm, t, a.tw_row);
     float2* f = a.field + ((size_t)slot * P + p) * H * W;
-    for_each_slot<G, K::RE>(t, [&](int s, int b, int n) {
-      const int row = row0 + b;
-      if (row < H) f[(size_t)row * W + n] = v[s];
-    });
+    if constexpr (TW == 0) {
+      for_each_slot<G, K::RE>(t, [&](int s, int b, int n) {
+        const int row = row0 + b;
+        if (row < H) f[(size_t)row * W + n] = v[s];
+      });
+    } else {
+      store_row_slots<K, K::RE, TW>(v, f, t, row0, H);
+    }
   }
 }
 

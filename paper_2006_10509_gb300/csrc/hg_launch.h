@@ -56,6 +56,10 @@ struct RowKernels {
   const void* mp_init[2];   // k_row_mp_init<PROJECT = false (gradient descent) / true (GS)>
   const void* mp[2];        // k_row_mp<OUT = false / true>
   const void* gd_bwd;       // k_row_gd_bwd
+  // multi-plane GS on a field tiled in column strips of width 2 / 4 / 8 (index as init_t; nullptr
+  // where the row length does not tile so, and for width 16): k_row_mp_init<PROJECT = true>, k_row_mp
+  const void* mp_init_t[4];
+  const void* mp_t[4][2];
   // generic lengths only (mp_init / mp / gd_bwd are nullptr there): multi-plane GS and gradient
   // descent run one launch per plane through a plan-owned accumulator [slot][H][W] complex64;
   // kernels (PassArgs, int plane, float* accumulator)

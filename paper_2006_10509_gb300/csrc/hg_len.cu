@@ -68,6 +68,26 @@ void set_tiled_alt_attrs() {
   }
 }
 
+// multi-plane GS row kernels on the tiled field (widths up to 8)
+template <int N, int TW>
+void fill_tiled_planes(RowKernels& r, int i) {
+  if constexpr (TW <= 8 && row_tileable<N, TW>()) {
+    r.mp_init_t[i] = (const void*)&k_row_mp_init<N, true, TW>;
+    r.mp_t[i][0] = (const void*)&k_row_mp<N, false, TW>;
+    r.mp_t[i][1] = (const void*)&k_row_mp<N, true, TW>;
+  }
+}
+
+template <int N, int TW>
+void set_tiled_planes_attrs() {
+  if constexpr (TW <= 8 && row_tileable<N, TW>()) {
+    constexpr int smem = RowCfg<N, TW>::SMEM;
+    allow_smem(&k_row_mp_init<N, true, TW>, smem);
+    allow_smem(&k_row_mp<N, false, TW>, smem);
+    allow_smem(&k_row_mp<N, true, TW>, smem);
+  }
+}
+
 template <int N, int TW>
 void set_tiled_attrs() {
   if constexpr (row_tileable<N, TW>()) {
@@ -123,6 +143,9 @@ RowKernels make_row() {
   fill_tiled_alt<N, 4>(r, 1);
   fill_tiled_alt<N, 8>(r, 2);
   fill_tiled_alt<N, 16>(r, 3);
+  fill_tiled_planes<N, 2>(r, 0);
+  fill_tiled_planes<N, 4>(r, 1);
+  fill_tiled_planes<N, 8>(r, 2);
   r.fft[0][0] = (const void*)&k_row_fft<N, false, false>;
   r.fft[0][1] = (const void*)&k_row_fft<N, false, true>;
   r.fft[1][0] = (const void*)&k_row_fft<N, true, false>;
@@ -225,6 +248,9 @@ void set_row_attrs(const RowKernels& r) {
   set_tiled_alt_attrs<HG_LEN, 4>();
   set_tiled_alt_attrs<HG_LEN, 8>();
   set_tiled_alt_attrs<HG_LEN, 16>();
+  set_tiled_planes_attrs<HG_LEN, 2>();
+  set_tiled_planes_attrs<HG_LEN, 4>();
+  set_tiled_planes_attrs<HG_LEN, 8>();
   allow_smem(&k_row_fft<HG_LEN, false, false>, r.smem);
   allow_smem(&k_row_fft<HG_LEN, false, true>, r.smem);
   allow_smem(&k_row_fft<HG_LEN, true, false>, r.smem);

@@ -96,16 +96,21 @@ def _run_item(hg, dev, plan, sizes, item, a, p):
 
 
 @pytest.mark.gpu
-def test_strip_width_rejected_for_multiplane_plans():
+def test_strip_widths_of_multiplane_plans():
+    """Multi-plane GS tiles its field in strips of 2, 4 or 8 columns (or keeps it row-major); the
+    16-column strips and the whole-run cluster kernel are single-plane only."""
     import paper_2006_10509_gb300 as hg
 
     with hg.Plan([256], [256], propagation=hg.HG_FRESNEL, wavelength_m=532e-9, pitch_m=8e-6,
                  z_m=[0.05, 0.1]) as plan:
-        assert plan.strip_width(0) == 0
-        with pytest.raises(hg.HologenError):
-            plan.set_strip_width(0, 2)
+        for w in (2, 4, 8, 0):
+            plan.set_strip_width(0, w)
+            assert plan.strip_width(0) == w
+        for w in (16, hg.HG_STRIP_CLUSTER):
+            with pytest.raises(hg.HologenError):
+                plan.set_strip_width(0, w)
         plan.autotune()
-        assert plan.strip_width(0) == 0
+        assert plan.strip_width(0) in (0, 2, 4, 8)
 
 
 # ------------------------------------------------------------------ radix plans

@@ -1,7 +1,7 @@
 """GPU parity of the multi-plane paths against the FP64 oracle.
 
-* Multi-plane GS (averaged projections over P Fresnel planes): one teacher-forced step, and the
-  plane-mean NMSE curve within 1 %.
+* Multi-plane GS (averaged projections over P Fresnel planes): one teacher-forced step on the
+  row-major field and on fields tiled in column strips, and the plane-mean NMSE curve within 1 %.
 * Gradient descent (hand-written Wirtinger adjoint): the GPU gradient against FP64 central finite
   differences of the oracle's loss (rel <= 1e-3, 64x64, P = 3) and against the oracle's analytic
   gradient (rel-L2 <= 1e-4); the loss per plane; Adam steps; the autograd front end.
@@ -35,20 +35,25 @@ def _intensity_targets(n, seed):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("levels", [0, 4])
-def test_multiplane_gs_one_step(levels):
+@pytest.mark.parametrize("levels,n,width", [(0, 64, None), (4, 64, None), (0, 256, 0), (0, 256, 2), (4, 256, 4),
+                                            (0, 256, 8), (4, 512, 2)])
+def test_multiplane_gs_one_step(levels, n, width):
+    """One step on the default field layout (width None), the row-major field (0) and fields tiled in
+    column strips of 2, 4 and 8."""
     import torch
 
     import paper_2006_10509_gb300 as hg
 
     dev = cuda_device()
-    n = 64
     amps = [np.sqrt(t) for t in _intensity_targets(n, 10)]
     cs = [optics.chirp(n, n, LAM, PITCH, z) for z in ZS]
     rng = np.random.default_rng(3)
     phi0 = (2 * np.pi * rng.integers(0, levels, (n, n)) / levels).astype(np.float32) if levels else \
         synth.uniform_phase(n, n, seed=4)
     with hg.Plan([n], [n], quant_levels=levels, **_fresnel(hg)) as plan:
+        if width is not None:
+            plan.set_strip_width(0, width)
+            assert plan.strip_width(0) == width
         ta = [torch.from_numpy(a).to(dev) for a in amps]
         tp = torch.from_numpy(phi0).to(dev)
         ph = torch.zeros((n, n), dtype=torch.float32, device=dev)
@@ -76,7 +81,8 @@ def test_multiplane_gs_one_step(levels):
 
 
 @pytest.mark.gpu
-def test_multiplane_gs_curve_256():
+@pytest.mark.parametrize("width", [None, 0])
+def test_multiplane_gs_curve_256(width):
     import torch
 
     import paper_2006_10509_gb300 as hg
@@ -87,6 +93,8 @@ def test_multiplane_gs_curve_256():
     cs = [optics.chirp(n, n, LAM, PITCH, z) for z in ZS]
     phi0 = synth.uniform_phase(n, n, seed=21)
     with hg.Plan([n], [n], **_fresnel(hg)) as plan:
+        if width is not None:
+            plan.set_strip_width(0, width)
         nm = torch.zeros((1, iters + 1), dtype=torch.float32, device=dev)
         plan.gs([torch.from_numpy(a).to(dev) for a in amps], iters, init_phase=[torch.from_numpy(phi0).to(dev)],
                 nmse_out=nm)
