@@ -268,58 +268,65 @@ __device__ __forceinline__ float2 init_unit(uint32_t p, uint64_t seed, int item)
 }
 
 // SLM projection (nearest point of the constraint set).  q receives the level index (quantised).
-__device__ __forceinline__ float2 slm_project(float2 g, int n_levels, const float2* __restrict__ lev, int& q) {
-  if (n_levels == 0) {
-    const float m2 = fmaf(g.x, g.x, g.y * g.y);
-    q = 0;
-    if (m2 > 0.f) {
-      const float r = rsqrtf(m2);
-      return make_float2(g.x * r, g.y * r);
-    }
-    return make_float2(1.f, 0.f);
+// One function per kind of phase-only SLM; slm_project picks one from the level count at run time,
+// slm_project_lv<LV> at compile time (LV = 0 continuous, 2, 4 or 8 the sector tests, -1 any other
+// count by the arctangent).
+
+__device__ __forceinline__ float2 project_continuous(float2 g, int& q) {
+  const float m2 = fmaf(g.x, g.x, g.y * g.y);
+  q = 0;
+  if (m2 > 0.f) {
+    const float r = rsqrtf(m2);
+    return make_float2(g.x * r, g.y * r);
   }
-  if (n_levels == 2) {
-    // arg in [pi/2, 3pi/2) -> pi; on Re g = 0, Im > 0 goes to pi and Im < 0 to 0
-    q = (g.x < 0.f || (g.x == 0.f && g.y > 0.f)) ? 1 : 0;
-    return make_float2(q ? -1.f : 1.f, 0.f);
+  return make_float2(1.f, 0.f);
+}
+
+__device__ __forceinline__ float2 project_binary(float2 g, int& q) {
+  // arg in [pi/2, 3pi/2) -> pi; on Re g = 0, Im > 0 goes to pi and Im < 0 to 0
+  q = (g.x < 0.f || (g.x == 0.f && g.y > 0.f)) ? 1 : 0;
+  return make_float2(q ? -1.f : 1.f, 0.f);
+}
+
+__device__ __forceinline__ float2 project_4(float2 g, const float2* __restrict__ lev, int& q) {
+  // levels 0, pi/2, pi, 3pi/2: the sector of g from |x| against |y| and the signs, no arctangent
+  // (measured on GB300: the 4-level GS row pass at 2048^2 29.8 -> 26.3 us).  A midpoint goes to
+  // the higher index: arg pi/4 -> 1, 3pi/4 -> 2, 5pi/4 -> 3, 7pi/4 -> 0.
+  const float ax = fabsf(g.x), ay = fabsf(g.y);
+  int qq;
+  if (ax > ay || (ax == ay && ((g.x > 0.f) != (g.y > 0.f))))
+    qq = g.x >= 0.f ? 0 : 2;
+  else
+    qq = g.y > 0.f ? 1 : 3;
+  if (ax == 0.f && ay == 0.f) qq = 0;
+  q = qq;
+  return __ldg(&lev[qq]);
+}
+
+__device__ __forceinline__ float2 project_8(float2 g, const float2* __restrict__ lev, int& q) {
+  // levels k pi/4: fold g into the first quadrant (quarter turns Q, (u, v) with u > 0, v >= 0),
+  // then the sector from v against tan(pi/8) u and u against tan(pi/8) v (a midpoint to the
+  // higher index, as above; g = 0 -> 0)
+  constexpr float t8 = 0.41421356237309504880f;  // tan(pi/8) = sqrt(2) - 1
+  int qd;
+  float u, v;
+  if (g.x > 0.f && g.y >= 0.f) {
+    qd = 0, u = g.x, v = g.y;
+  } else if (g.x <= 0.f && g.y > 0.f) {
+    qd = 1, u = g.y, v = -g.x;
+  } else if (g.x < 0.f && g.y <= 0.f) {
+    qd = 2, u = -g.x, v = -g.y;
+  } else {
+    qd = 3, u = -g.y, v = g.x;
   }
-  if (n_levels == 4) {
-    // levels 0, pi/2, pi, 3pi/2: the sector of g from |x| against |y| and the signs, no arctangent
-    // (measured on GB300: the 4-level GS row pass at 2048^2 29.8 -> 26.3 us).  A midpoint goes to
-    // the higher index: arg pi/4 -> 1, 3pi/4 -> 2, 5pi/4 -> 3, 7pi/4 -> 0.  Other level counts use
-    // the arctangent below; 8 levels the quadrant folding that follows.
-    const float ax = fabsf(g.x), ay = fabsf(g.y);
-    int qq;
-    if (ax > ay || (ax == ay && ((g.x > 0.f) != (g.y > 0.f))))
-      qq = g.x >= 0.f ? 0 : 2;
-    else
-      qq = g.y > 0.f ? 1 : 3;
-    if (ax == 0.f && ay == 0.f) qq = 0;
-    q = qq;
-    return __ldg(&lev[qq]);
-  }
-  if (n_levels == 8) {
-    // levels k pi/4: fold g into the first quadrant (quarter turns Q, (u, v) with u > 0, v >= 0),
-    // then the sector from v against tan(pi/8) u and u against tan(pi/8) v (a midpoint to the
-    // higher index, as above; g = 0 -> 0)
-    constexpr float t8 = 0.41421356237309504880f;  // tan(pi/8) = sqrt(2) - 1
-    int qd;
-    float u, v;
-    if (g.x > 0.f && g.y >= 0.f) {
-      qd = 0, u = g.x, v = g.y;
-    } else if (g.x <= 0.f && g.y > 0.f) {
-      qd = 1, u = g.y, v = -g.x;
-    } else if (g.x < 0.f && g.y <= 0.f) {
-      qd = 2, u = -g.x, v = -g.y;
-    } else {
-      qd = 3, u = -g.y, v = g.x;
-    }
-    int qq = 2 * qd + (v < t8 * u ? 0 : (t8 * v >= u ? 2 : 1));
-    if (qq >= 8) qq -= 8;
-    if (g.x == 0.f && g.y == 0.f) qq = 0;
-    q = qq;
-    return __ldg(&lev[qq]);
-  }
+  int qq = 2 * qd + (v < t8 * u ? 0 : (t8 * v >= u ? 2 : 1));
+  if (qq >= 8) qq -= 8;
+  if (g.x == 0.f && g.y == 0.f) qq = 0;
+  q = qq;
+  return __ldg(&lev[qq]);
+}
+
+__device__ __forceinline__ float2 project_levels(float2 g, int n_levels, const float2* __restrict__ lev, int& q) {
   const float a = atan2f(g.y, g.x);  // (-pi, pi]
   float t = a * ((float)n_levels * 0.15915494309189533577f);
   if (t < 0.f) t += (float)n_levels;
@@ -327,6 +334,47 @@ __device__ __forceinline__ float2 slm_project(float2 g, int n_levels, const floa
   if (qq >= n_levels) qq -= n_levels;
   q = qq;
   return __ldg(&lev[qq]);
+}
+
+template <int LV>
+__device__ __forceinline__ float2 slm_project_lv(float2 g, int n_levels, const float2* __restrict__ lev, int& q) {
+  if constexpr (LV == 0)
+    return project_continuous(g, q);
+  else if constexpr (LV == 2)
+    return project_binary(g, q);
+  else if constexpr (LV == 4)
+    return project_4(g, lev, q);
+  else if constexpr (LV == 8)
+    return project_8(g, lev, q);
+  else
+    return project_levels(g, n_levels, lev, q);
+}
+
+__device__ __forceinline__ float2 slm_project(float2 g, int n_levels, const float2* __restrict__ lev, int& q) {
+  if (n_levels == 0) return project_continuous(g, q);
+  if (n_levels == 2) return project_binary(g, q);
+  if (n_levels == 4) return project_4(g, lev, q);
+  if (n_levels == 8) return project_8(g, lev, q);
+  return project_levels(g, n_levels, lev, q);
+}
+
+// Calls f(std::integral_constant<int, LV>) with LV the compile-time projection kind of a run's
+// phase-only level count: the kernels whose pixel loops project take the choice once per launch.
+// (The run-time choice inside the unrolled loops of the GS row pass cost about three branches per
+// pixel and instruction-fetch stalls: measured on GB300, 2048^2 continuous row pass 26.4 us against
+// 24.4 us before the 8-level branch was added to it.)
+template <class F>
+__device__ __forceinline__ void dispatch_levels(int n_levels, F&& f) {
+  if (n_levels == 0)
+    f(std::integral_constant<int, 0>{});
+  else if (n_levels == 2)
+    f(std::integral_constant<int, 2>{});
+  else if (n_levels == 4)
+    f(std::integral_constant<int, 4>{});
+  else if (n_levels == 8)
+    f(std::integral_constant<int, 8>{});
+  else
+    f(std::integral_constant<int, -1>{});
 }
 
 // Multi-amplitude / complex-modulation SLM: the nearest of the m complex values lev[0..m) (squared
@@ -601,10 +649,11 @@ __global__ void __launch_bounds__(RowCfg<W, TW, PV>::NT, RowCfg<W, TW, PV>::MINB
   // a multi-amplitude SLM's projection depends on the scale of g: bring the unnormalised field to
   // the unitary scale of the loop (replay target at a unit-modulus field's energy): 1 / sqrt(sum A^2)
   // for GS, 1 / (H W) under MRAF / HIO, whose column pass already scales the replacement
-  // the table branch is taken once per launch, outside the pixel loop (measured: a per-pixel test
-  // cost MRAF 8 % and HIO 11 % at 2048^2)
-  auto pointwise = [&](auto table) {
+  // the table branch and the projection kind are chosen once per launch, outside the pixel loop
+  // (measured: a per-pixel table test cost MRAF 8 % and HIO 11 % at 2048^2)
+  auto pointwise = [&](auto table, auto lv) {
     constexpr bool TABLE = decltype(table)::value;
+    constexpr int LV = decltype(lv)::value;
     const float gscale = TABLE ? (a.mix > 0.f ? 1.f / ((float)H * (float)W)
                                               : (float)__ldcg(&a.stats[(size_t)a.class_slot[k] * 4 + 3]))
                                : 1.f;
@@ -618,7 +667,7 @@ __global__ void __launch_bounds__(RowCfg<W, TW, PV>::NT, RowCfg<W, TW, PV>::MINB
       }
       int q;
       float2 h = TABLE ? table_project(c_scale(g, gscale), -a.n_levels, a.lev, q)
-                       : slm_project(g, a.n_levels, a.lev, q);
+                       : slm_project_lv<LV>(g, a.n_levels, a.lev, q);
       if (OUT && row < H) {
         const size_t p = (size_t)row * W + n;
         if (po) po[p] = a.n_levels ? __ldg(&a.lev_phase[q]) : phase_0_2pi(h);
@@ -630,9 +679,9 @@ __global__ void __launch_bounds__(RowCfg<W, TW, PV>::NT, RowCfg<W, TW, PV>::MINB
     });
   };
   if (EXT && a.n_levels < 0)
-    pointwise(std::true_type{});
+    pointwise(std::true_type{}, std::integral_constant<int, 0>{});
   else
-    pointwise(std::false_type{});
+    dispatch_levels(a.n_levels, [&](auto lv) { pointwise(std::false_type{}, lv); });
   FftRun<G, false, 1, typename K::Fwd, typename K::Fwd>::run(v, sm, t, a.tw_row);
   // tiled: re-derive the (run-time stride) store addresses rather than keep the load's live
   if (TW)
@@ -1082,16 +1131,18 @@ __global__ void __launch_bounds__(RowCfg<W, TW>::NT, TW ? hg_max(1, 512 / RowCfg
   }
   float* po = OUT ? a.phase_out[k] : nullptr;
   uint8_t* lo = OUT ? a.level_out[k] : nullptr;
-  for_each_slot<G, K::RM>(t, [&](int s, int b, int n) {
-    const int row = row0 + b;
-    int q;
-    const float2 h = slm_project(g[s], a.n_levels, a.lev, q);
-    if (OUT && row < H) {
-      const size_t px = (size_t)row * W + n;
-      if (po) po[px] = a.n_levels ? __ldg(&a.lev_phase[q]) : phase_0_2pi(h);
-      if (lo) lo[px] = (uint8_t)q;
-    }
-    g[s] = row < H ? h : make_float2(0.f, 0.f);
+  dispatch_levels(a.n_levels, [&](auto lv) {
+    for_each_slot<G, K::RM>(t, [&](int s, int b, int n) {
+      const int row = row0 + b;
+      int q;
+      const float2 h = slm_project_lv<decltype(lv)::value>(g[s], a.n_levels, a.lev, q);
+      if (OUT && row < H) {
+        const size_t px = (size_t)row * W + n;
+        if (po) po[px] = a.n_levels ? __ldg(&a.lev_phase[q]) : phase_0_2pi(h);
+        if (lo) lo[px] = (uint8_t)q;
+      }
+      g[s] = row < H ? h : make_float2(0.f, 0.f);
+    });
   });
   for (int p = 0; p < P; ++p) {
     float2 v[K::V];
@@ -1361,23 +1412,25 @@ __global__ void __launch_bounds__(ClusterCfg<N, CL>::NT, 1) k_gs_cluster(const _
     for_each_slot<GR, RFirst<Inv>::value>(t, [&](int s, int b, int n) { v[s] = fld[b * N + n]; });
     FftRun<GR, true, 1, Inv>::run(v, xs, t, a.tw_row);
     const bool out = it == n_iter - 1;
-    for_each_slot<GR, RFirst<Fwd>::value>(t, [&](int s, int b, int n) {
-      const int row = row0 + b;
-      float2 g = v[s];
-      float2 c = make_float2(1.f, 0.f);
-      if (a.cx) {
-        c = c_mul(__ldg(&a.cx[n]), __ldg(&a.cy[row]));
-        g = c_mulc(g, c);
-      }
-      int q;
-      float2 h = slm_project(g, a.n_levels, a.lev, q);
-      if (out) {
-        const size_t p = (size_t)row * N + n;
-        if (po) po[p] = a.n_levels ? __ldg(&a.lev_phase[q]) : phase_0_2pi(h);
-        if (lo) lo[p] = (uint8_t)q;
-      }
-      if (a.cx) h = c_mul(h, c);
-      v[s] = h;
+    dispatch_levels(a.n_levels, [&](auto lv) {
+      for_each_slot<GR, RFirst<Fwd>::value>(t, [&](int s, int b, int n) {
+        const int row = row0 + b;
+        float2 g = v[s];
+        float2 c = make_float2(1.f, 0.f);
+        if (a.cx) {
+          c = c_mul(__ldg(&a.cx[n]), __ldg(&a.cy[row]));
+          g = c_mulc(g, c);
+        }
+        int q;
+        float2 h = slm_project_lv<decltype(lv)::value>(g, a.n_levels, a.lev, q);
+        if (out) {
+          const size_t p = (size_t)row * N + n;
+          if (po) po[p] = a.n_levels ? __ldg(&a.lev_phase[q]) : phase_0_2pi(h);
+          if (lo) lo[p] = (uint8_t)q;
+        }
+        if (a.cx) h = c_mul(h, c);
+        v[s] = h;
+      });
     });
     FftRun<GR, false, 1, Fwd>::run(v, xs, t, a.tw_row);
     for_each_slot<GR, RLast<Fwd>::value>(t, [&](int s, int b, int n) { fld[b * N + n] = v[s]; });
