@@ -529,24 +529,33 @@ struct Geo {
     return nbf<R>() % NT == 0;
   }
 
-  // Shared-memory slot of element (b, n), padded by one float2 per 16: the Stockham stores of a stage
-  // with stride R (R = 4, 8, 16) land on distinct banks within each half-warp.  Interleaved row tiles
-  // also swizzle row b by (16 / B) b within each 16-element block, so that the B rows a warp touches
-  // at once start on different banks.
-  static constexpr int SWZ = B >= 16 ? 1 : 16 / B;
-  // ALT: the layout of the exchange after a radix-8 first stage (each thread stores 8 consecutive
-  // values).  For 2-row tiles the 8 b swizzle leaves that exchange 2-way conflicted and 12 b makes
-  // it conflict-free (measured: row pass 31.2 -> 29.9 us at 2048).  Column strips keep their layout
+  // Shared-memory slot of element (b, n) in an exchange of layout LAY (exchange_layout below).
+  // LAY 0 pads by one float2 per 16: the Stockham stores of a power-of-two radix R = 4, 8, 16 after
+  // a power-of-two number of points land on distinct banks within each half-warp.  Interleaved row
+  // tiles also swizzle row b by (16 / B) b within each 16-element block, so that the B rows a warp
+  // touches at once start on different banks.
+  // LAY 1: the exchange after a radix-8 first stage (each thread stores 8 consecutive values).  For
+  // 2-row tiles the 8 b swizzle leaves that exchange 2-way conflicted and 12 b makes it
+  // conflict-free (measured: row pass 31.2 -> 29.9 us at 2048).  Column strips keep their layout
   // (a row-style one removes the conflicts there too, but measured no faster).
+  // LAY 2: unpadded (swizzle kept), for exchanges whose radix or point count is odd (3, 5, 9, 15) or
+  // whose radix is not a power of two (6, 12): an odd store stride already meets every bank within a
+  // half-warp, and the padding then folds strides onto one another (modelled for every plan and tile
+  // shape: 1920-point row tiles after a radix-15 first stage 6-8x the ideal wavefronts padded, 1x
+  // unpadded).
+  static constexpr int SWZ = B >= 16 ? 1 : 16 / B;
   static constexpr bool ROW_ALT = B == 2 && !COLS;
-  template <bool ALT = false>
+  template <int LAY = 0>
   __device__ __forceinline__ static int sidx(int b, int n) {
     int i;
-    if constexpr (ALT && ROW_ALT)
+    if constexpr (LAY == 1 && ROW_ALT)
       i = ILV ? b * N + (n ^ (12 * b)) : b * N + n;
     else
       i = COLS ? n * B + b : (ILV ? b * N + (n ^ (SWZ * b)) : b * N + n);
-    return i + (i >> 4);
+    if constexpr (LAY == 2)
+      return i;
+    else
+      return i + (i >> 4);
   }
   // float2 slots of the exchange buffer, rounded up to 128 bytes so that data placed after it is
   // 16-byte aligned (cp.async destinations)
@@ -636,53 +645,58 @@ __device__ __forceinline__ void stage_compute(float2 (&v)[V], int t, const float
 
 // Slot index steps of a stage: element n + r * STEP for r = 0..R-1.  When the step in the unpadded
 // index (STEP, times B in a column strip) is a multiple of 16, the padded (and swizzled) slot of
-// n + r * STEP is the slot of n plus r * 17 * step / 16, so one index is computed per butterfly.
-template <class G, int STEP, bool ALT = false>
+// n + r * STEP is the slot of n plus r * 17 * step / 16, so one index is computed per butterfly; an
+// unpadded layout steps by the raw index (for interleaved row tiles only when the step leaves the
+// swizzled low four bits alone).  -1: no constant step.
+template <class G, int STEP, int LAY = 0>
 __host__ __device__ constexpr int padded_step() {
   constexpr int raw = G::COLS ? STEP * G::B : STEP;
+  if constexpr (LAY == 2) return (!G::ILV || STEP % 16 == 0) ? raw : -1;
   return raw % 16 == 0 ? raw / 16 * 17 : -1;
 }
 
-// The exchange after stage (R, NS) uses the ALT layout when that stage is a radix-8 first stage.
+// Layout of the exchange after stage (R, NS) (Geo::sidx): 1 after a radix-8 first stage, 2 when R
+// is not a power of two or NS is odd and above 1, else 0.
 template <int R, int NS>
-__host__ __device__ constexpr bool alt_exchange() {
-  return R == 8 && NS == 1;
+__host__ __device__ constexpr int exchange_layout() {
+  if (R == 8 && NS == 1) return 1;
+  return ((R & (R - 1)) != 0 || (NS > 1 && NS % 2 == 1)) ? 2 : 0;
 }
 
 template <class G, int R, int NS, int V>
 __device__ __forceinline__ void stage_store(const float2 (&v)[V], float2* sm, int t) {
-  constexpr bool ALT = alt_exchange<R, NS>();
-  constexpr int PS = padded_step<G, NS, ALT>();
+  constexpr int LAY = exchange_layout<R, NS>();
+  constexpr int PS = padded_step<G, NS, LAY>();
 #pragma unroll
   for (int i = 0; i < G::template bpt<R>(); ++i) {
     int b, j;
     if (!G::template bf<R>(t, i, b, j)) continue;
     const int base = (j / NS) * NS * R + (j % NS);
     if constexpr (PS > 0) {
-      float2* q = sm + G::template sidx<ALT>(b, base);
+      float2* q = sm + G::template sidx<LAY>(b, base);
 #pragma unroll
       for (int r = 0; r < R; ++r) q[r * PS] = v[i * R + r];
     } else {
 #pragma unroll
-      for (int r = 0; r < R; ++r) sm[G::template sidx<ALT>(b, base + r * NS)] = v[i * R + r];
+      for (int r = 0; r < R; ++r) sm[G::template sidx<LAY>(b, base + r * NS)] = v[i * R + r];
     }
   }
 }
 
-template <class G, int R, bool ALT, int V>
+template <class G, int R, int LAY, int V>
 __device__ __forceinline__ void stage_load(float2 (&v)[V], const float2* sm, int t) {
-  constexpr int PS = padded_step<G, G::N / R, ALT>();
+  constexpr int PS = padded_step<G, G::N / R, LAY>();
 #pragma unroll
   for (int i = 0; i < G::template bpt<R>(); ++i) {
     int b, j;
     if (!G::template bf<R>(t, i, b, j)) continue;
     if constexpr (PS > 0) {
-      const float2* q = sm + G::template sidx<ALT>(b, j);
+      const float2* q = sm + G::template sidx<LAY>(b, j);
 #pragma unroll
       for (int r = 0; r < R; ++r) v[i * R + r] = q[r * PS];
     } else {
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[i * R + r] = sm[G::template sidx<ALT>(b, j + r * (G::N / R))];
+      for (int r = 0; r < R; ++r) v[i * R + r] = sm[G::template sidx<LAY>(b, j + r * (G::N / R))];
     }
   }
 }
@@ -701,7 +715,7 @@ struct FftRun<G, INV, NS, RList<R, Rs...>, F> {
       __syncthreads();  // everyone is done reading sm from the previous exchange
       stage_store<G, R, NS>(v, sm, t);
       __syncthreads();
-      stage_load<G, RFirst<RList<Rs...>>::value, alt_exchange<R, NS>()>(v, sm, t);
+      stage_load<G, RFirst<RList<Rs...>>::value, exchange_layout<R, NS>()>(v, sm, t);
       FftRun<G, INV, NS * R, RList<Rs...>, F>::run(v, sm, t, tw);
     }
   }

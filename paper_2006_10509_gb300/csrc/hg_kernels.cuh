@@ -997,9 +997,23 @@ __global__ void __launch_bounds__(RowCfg<W>::NT) k_row_ospr(const __grid_constan
         const int row = row0 + b;
         if (row >= H) continue;
         uint32_t x = 0;
-        for (int i = 0; i < 32; ++i) {
-          const int n = word * 32 + i;
-          if (n < W) x |= (uint32_t)qs[b * W + n] << i;
+        if constexpr (W % 16 == 0) {
+          // the word's 32 decisions (bytes 0 / 1) as two 16-byte loads, four bits from each 32-bit
+          // lane by shifts (measured on GB300, 1920-pixel rows: one byte load per decision was 8-way
+          // bank-conflicted); with W a multiple of 16 a half-word is either whole or past the row
+          auto pack4 = [](uint32_t u) { return (u | (u >> 7) | (u >> 14) | (u >> 21)) & 0xFu; };
+          const uint4* src = reinterpret_cast<const uint4*>(qs + b * W + word * 32);
+          const uint4 lo = src[0];
+          x = pack4(lo.x) | pack4(lo.y) << 4 | pack4(lo.z) << 8 | pack4(lo.w) << 12;
+          if (word * 32 + 16 < W) {
+            const uint4 hi = src[1];
+            x |= (pack4(hi.x) | pack4(hi.y) << 4 | pack4(hi.z) << 8 | pack4(hi.w) << 12) << 16;
+          }
+        } else {
+          for (int i = 0; i < 32; ++i) {
+            const int n = word * 32 + i;
+            if (n < W) x |= (uint32_t)qs[b * W + n] << i;
+          }
         }
         dst[(size_t)row * WORDS + word] = x;
       }
