@@ -1709,7 +1709,7 @@ hg_status hg_ospr_run(hg_plan* p, const float* const* target_amp, int32_t n_subf
         a.ttile = c.ttile;
         ag.ttile = c.ttile;
         a.iter = 0;
-        if ((s = launch(p, K_COL_OSPR, c.ck->ospr[0], gcol, c.ck->nt, c.ck->smem_gs, a, st)) != HG_OK) return s;
+        if ((s = launch(p, K_COL_OSPR, c.ck->ospr[0], gcol, c.ck->nt, c.ck->smem_ospr, a, st)) != HG_OK) return s;
         for (int sf = 0; sf < n_subframes; ++sf) {
           a.iter = sf;
           hg::PassArgs ar = a;  // the first row pass of subframe sf adds up NMSE[sf - 1]
@@ -1724,7 +1724,7 @@ hg_status hg_ospr_run(hg_plan* p, const float* const* target_amp, int32_t n_subf
           a.iter = sf + 1;
           a.acc_read = sf > 0;
           const int variant = sf + 1 < n_subframes ? 1 : 2;
-          if ((s = launch(p, K_COL_OSPR, c.ck->ospr[variant], gcol, c.ck->nt, c.ck->smem_gs, a, st)) != HG_OK)
+          if ((s = launch(p, K_COL_OSPR, c.ck->ospr[variant], gcol, c.ck->nt, c.ck->smem_ospr, a, st)) != HG_OK)
             return s;
         }
         a.fin_iter = n_subframes - 1;

@@ -749,6 +749,7 @@ std::unique_ptr<Tables> make_tables(int n) {
   c.nt = threads(t->pcol);
   c.smem = padded(cols * n) * (int)sizeof(float2);
   c.smem_gs = c.smem;
+  c.smem_ospr = c.smem;
   c.gs[0][0] = c.gs[0][1] = (const void*)&kg_col_gs<false>;
   c.gs[1][0] = c.gs[1][1] = (const void*)&kg_col_gs<true>;
   c.tile = 0;

@@ -93,6 +93,10 @@ struct ColCfg {
   static constexpr int V = MaxV<G, Fwd>::value;
   static constexpr int SMEM = G::SM_ELEMS * 8;
   static constexpr int SMEM_T = SMEM + H * C * 4;  // + the strip's target values (GS passes)
+  // the OSPR column pass also stages the strip's accumulated intensity where that keeps at least
+  // two CTAs per SM (80 KB); otherwise it reads the sum from global memory where it adds to it
+  static constexpr bool OSPR_ACC_SM = SMEM_T + H * C * 4 <= 80 * 1024;
+  static constexpr int SMEM_OSPR = OSPR_ACC_SM ? SMEM_T + H * C * 4 : SMEM_T;
   static constexpr int MINB = hg_max(1, 1024 / NT);  // CTAs per SM the register budget is cut for
   // the configuration exists: no thread past the value budget, the GS pass's shared memory fits
   static constexpr bool FEASIBLE =
@@ -884,8 +888,10 @@ __device__ __forceinline__ float2 random_field(uint32_t p, int s, uint64_t seed,
 
 // FINISH: the field holds rowFFT(h_{s-1} c); accumulate its replay intensity (ACC_READ: add to the
 // stored sum, else start it) and write NMSE[s-1].  START: build subframe s and inverse-transform it.
-// The strip's target comes from the tiled copy (a.ttile, prefetched into shared memory) and the
-// accumulated intensity is kept per strip ([strip][H][C], a.acc), so both stream contiguously.
+// The strip's target comes from the tiled copy (a.ttile) and the accumulated intensity is kept per
+// strip ([strip][H][C], a.acc), so both stream contiguously; both are prefetched into shared memory
+// while the forward transform runs (measured on GB300, 1080 x 1920: the sum read where it is added
+// left the pass waiting on global loads, 4.97 cycles per issue).
 template <int H, bool FINISH, bool START>
 __global__ void __launch_bounds__(ColCfg<H>::NT, ColCfg<H>::MINB) k_col_ospr(const __grid_constant__ PassArgs a) {
   using K = ColCfg<H>;
@@ -899,7 +905,10 @@ __global__ void __launch_bounds__(ColCfg<H>::NT, ColCfg<H>::MINB) k_col_ospr(con
   const size_t strip = ((size_t)slot * gridDim.x + blockIdx.x) * H * K::C;
   float* acc = a.acc + strip;
   float* ts = reinterpret_cast<float*>(sm + G::SM_ELEMS);  // the strip's target, [n][C]
+  float* as = ts + H * K::C;                                 // the strip's accumulated intensity
+  static_assert((H * K::C) % 4 == 0, "16-byte strip copies");
   prefetch_contig<H * K::C, K::NT>(ts, a.ttile + strip);
+  if (K::OSPR_ACC_SM && FINISH && a.acc_read) prefetch_contig<H * K::C, K::NT>(as, acc);
   float2 v[K::V];
   float s_it = 0.f, s_ii = 0.f, s_tt = 0.f;
   if (FINISH) {
@@ -909,14 +918,14 @@ __global__ void __launch_bounds__(ColCfg<H>::NT, ColCfg<H>::MINB) k_col_ospr(con
     });
     FftRun<G, false, 1, typename K::Fwd>::run(v, sm, t, a.tw_col);
     cp_async_wait_all();
-    __syncthreads();  // the target strip has landed
+    __syncthreads();  // the target (and accumulated-intensity) strips have landed
     for_each_slot<G, RLast<typename K::Fwd>::value>(t, [&](int s, int b, int n) {
       const int col = col0 + b;
       if (col < W) {
         const int p = n * K::C + b;
         const float2 r = v[s];
         float i2 = fmaf(r.x, r.x, r.y * r.y);
-        if (a.acc_read) i2 += acc[p];
+        if (a.acc_read) i2 += K::OSPR_ACC_SM ? as[p] : acc[p];
         acc[p] = i2;
         const float amp = ts[p];
         const float tt = amp * amp;

@@ -83,7 +83,8 @@ struct ColKernels {
   int cols;                 // strip width on a row-major field (all kernels but gs_t)
   int nt;
   int smem;
-  int smem_gs;              // dynamic shared memory of k_col_gs / k_col_ospr (exchange + target strip)
+  int smem_gs;              // dynamic shared memory of k_col_gs (exchange + target strip)
+  int smem_ospr;            // of k_col_ospr (exchange + target strip + accumulated-intensity strip)
   // [EXT]: the plain kernel, or the one that also takes the signal / noise regions of MRAF and HIO
   const void* gs[2][2];     // k_col_gs<REPLACE = false / true> (row-major field)
   // k_col_gs on the GS field tiled in strips of width 2 / 4 / 8 / 16 (gs nullptr where that

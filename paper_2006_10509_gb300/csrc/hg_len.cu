@@ -209,6 +209,7 @@ ColKernels make_col() {
   c.nt = K::NT;
   c.smem = K::SMEM;
   c.smem_gs = K::SMEM_T;
+  c.smem_ospr = K::SMEM_OSPR;
   c.gs[0][0] = (const void*)&k_col_gs<N, false, 0, false>;
   c.gs[0][1] = (const void*)&k_col_gs<N, false, 0, true>;
   c.gs[1][0] = (const void*)&k_col_gs<N, true, 0, false>;
@@ -279,9 +280,9 @@ void set_col_attrs(const ColKernels& c) {
   allow_smem(&k_col_fft<HG_LEN, false, true>, c.smem);
   allow_smem(&k_col_fft<HG_LEN, true, false>, c.smem);
   allow_smem(&k_col_fft<HG_LEN, true, true>, c.smem);
-  allow_smem(&k_col_ospr<HG_LEN, false, true>, c.smem_gs);
-  allow_smem(&k_col_ospr<HG_LEN, true, true>, c.smem_gs);
-  allow_smem(&k_col_ospr<HG_LEN, true, false>, c.smem_gs);
+  allow_smem(&k_col_ospr<HG_LEN, false, true>, c.smem_ospr);
+  allow_smem(&k_col_ospr<HG_LEN, true, true>, c.smem_ospr);
+  allow_smem(&k_col_ospr<HG_LEN, true, false>, c.smem_ospr);
   allow_smem(&k_col_gd<HG_LEN, false>, c.smem);
   allow_smem(&k_col_gd<HG_LEN, true>, c.smem);
 }
