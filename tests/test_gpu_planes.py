@@ -103,6 +103,43 @@ def test_multiplane_gs_curve_256(width):
     check_nmse(nm.cpu().numpy()[0], ref["nmse"])
 
 
+@pytest.mark.gpu
+def test_multiplane_gs_mixed_size_batch_matches_single_items():
+    """Items of two sizes in one multi-plane plan (each size class on its own field layout, targets
+    re-laid out per item and plane): every item's phase and NMSE curve equal those of a one-item
+    plan bit for bit, and the start's NMSE matches the oracle."""
+    import torch
+
+    import paper_2006_10509_gb300 as hg
+
+    dev = cuda_device()
+    sizes, zs, iters = [256, 512, 256], (0.08, 0.12), 3
+    amps = [[np.sqrt(t) for t in _intensity_targets(n, 30 + 10 * i)[:2]] for i, n in enumerate(sizes)]
+    phis = [synth.uniform_phase(n, n, seed=31 + 10 * i) for i, n in enumerate(sizes)]
+
+    def run(plan, items):
+        ta = [torch.from_numpy(a).to(dev) for i in items for a in amps[i]]
+        tp = [torch.from_numpy(phis[i]).to(dev) for i in items]
+        ph = [torch.zeros((sizes[i], sizes[i]), dtype=torch.float32, device=dev) for i in items]
+        nm = torch.zeros((len(items), iters + 1), dtype=torch.float32, device=dev)
+        plan.gs(ta, iters, init_phase=tp, phase_out=ph, nmse_out=nm)
+        plan.sync()
+        return [x.cpu().numpy() for x in ph], nm.cpu().numpy()
+
+    with hg.Plan(sizes, sizes, **_fresnel(hg, zs)) as plan:
+        widths = [plan.strip_width(i) for i in range(3)]
+        ph_b, nm_b = run(plan, [0, 1, 2])
+    for i, n in enumerate(sizes):
+        with hg.Plan([n], [n], **_fresnel(hg, zs)) as plan:
+            assert plan.strip_width(0) == widths[i]
+            ph1, nm1 = run(plan, [i])
+        assert np.array_equal(ph1[0], ph_b[i])
+        assert np.array_equal(nm1[0], nm_b[i])
+    cs = [optics.chirp(512, 512, LAM, PITCH, z) for z in zs]
+    ref = ogs.multiplane_gs([a.astype(np.float64) for a in amps[1]], phis[1].astype(np.float64), 1, cs)
+    check_nmse(nm_b[1][:1], ref["nmse"][:1], rtol=1e-3)
+
+
 # ------------------------------------------------------------------ gradient descent
 
 
