@@ -1010,6 +1010,11 @@ hg_status gs_class(hg_plan* p, const SizeClass& c, const GsCall& g, cudaStream_t
     const int csm = pcol ? c.ck->tiled[ti].smem_gs_p : (tiled ? c.ck->tiled[ti].smem_gs : c.ck->smem_gs);
     if (prow) a.tw_row = p->tw_alt.at(c.W);
     if (pcol) a.tw_col = p->tw_alt.at(c.H);
+    // square items on 2-column strips: the row pass instance with the strip height at compile time
+    if (tiled && width == 2 && x == 0 && c.H == c.W && c.rk->gs_sq[prow ? 1 : 0][0] != nullptr) {
+      k_row[0] = c.rk->gs_sq[prow ? 1 : 0][0];
+      k_row[1] = c.rk->gs_sq[prow ? 1 : 0][1];
+    }
     const dim3 grow((c.H + rrows - 1) / rrows, nb), gcol(strips, nb);
     // prologue (writes h_0 out when there is no iteration)
     hg::PassArgs a0 = a;

@@ -50,6 +50,9 @@ struct RowKernels {
   const void* gs_tp[4][2];
   int nt_tp[4], smem_tp[4];
   TwiddleLayout tw_alt;     // twiddle tables of the alternative plan
+  // the plain GS row pass on 2-column strips for square items (strip height W at compile time):
+  // [radix plan 0 / 1][OUT = false / true]; nullptr where that instance does not exist
+  const void* gs_sq[2][2];
   const void* fft[2][2];    // k_row_fft<INV><PRE>
   const void* ospr[2];      // k_row_ospr<BITS = false / true>
   int smem_ospr;            // dynamic shared memory of k_row_ospr (field tile + bit decisions)

@@ -59,6 +59,31 @@ void fill_tiled_alt(RowKernels& r, int i) {
   }
 }
 
+// the plain row pass on 2-column strips for square items, both radix plans
+template <int N>
+void fill_square(RowKernels& r) {
+  if constexpr (row_tileable<N, 2>()) {
+    r.gs_sq[0][0] = (const void*)&k_row_gs<N, false, 2, false, 0, true>;
+    r.gs_sq[0][1] = (const void*)&k_row_gs<N, true, 2, false, 0, true>;
+  }
+  if constexpr (has_alt_plan<N>() && row_tileable<N, 2, 1>()) {
+    r.gs_sq[1][0] = (const void*)&k_row_gs<N, false, 2, false, 1, true>;
+    r.gs_sq[1][1] = (const void*)&k_row_gs<N, true, 2, false, 1, true>;
+  }
+}
+
+template <int N>
+void set_square_attrs() {
+  if constexpr (row_tileable<N, 2>()) {
+    allow_smem(&k_row_gs<N, false, 2, false, 0, true>, RowCfg<N, 2>::SMEM);
+    allow_smem(&k_row_gs<N, true, 2, false, 0, true>, RowCfg<N, 2>::SMEM);
+  }
+  if constexpr (has_alt_plan<N>() && row_tileable<N, 2, 1>()) {
+    allow_smem(&k_row_gs<N, false, 2, false, 1, true>, RowCfg<N, 2, 1>::SMEM);
+    allow_smem(&k_row_gs<N, true, 2, false, 1, true>, RowCfg<N, 2, 1>::SMEM);
+  }
+}
+
 template <int N, int TW>
 void set_tiled_alt_attrs() {
   if constexpr (has_alt_plan<N>() && row_tileable<N, TW, 1>()) {
@@ -146,6 +171,7 @@ RowKernels make_row() {
   fill_tiled_planes<N, 2>(r, 0);
   fill_tiled_planes<N, 4>(r, 1);
   fill_tiled_planes<N, 8>(r, 2);
+  fill_square<N>(r);
   r.fft[0][0] = (const void*)&k_row_fft<N, false, false>;
   r.fft[0][1] = (const void*)&k_row_fft<N, false, true>;
   r.fft[1][0] = (const void*)&k_row_fft<N, true, false>;
@@ -252,6 +278,7 @@ void set_row_attrs(const RowKernels& r) {
   set_tiled_planes_attrs<HG_LEN, 2>();
   set_tiled_planes_attrs<HG_LEN, 4>();
   set_tiled_planes_attrs<HG_LEN, 8>();
+  set_square_attrs<HG_LEN>();
   allow_smem(&k_row_fft<HG_LEN, false, false>, r.smem);
   allow_smem(&k_row_fft<HG_LEN, false, true>, r.smem);
   allow_smem(&k_row_fft<HG_LEN, true, false>, r.smem);
