@@ -935,6 +935,10 @@ hg_status gs_class(hg_plan* p, const SizeClass& c, const GsCall& g, cudaStream_t
           gcol(strips, nb * P);
       const void* k_init = tiled ? c.rk->mp_init_t[ti] : c.rk->mp_init[1];
       const void* k_row[2] = {tiled ? c.rk->mp_t[ti][0] : c.rk->mp[0], tiled ? c.rk->mp_t[ti][1] : c.rk->mp[1]};
+      if (tiled && width == 2 && c.H == c.W && c.rk->mp_sq[0] != nullptr) {  // square: compile-time strip height
+        k_row[0] = c.rk->mp_sq[0];
+        k_row[1] = c.rk->mp_sq[1];
+      }
       const void* k_col[2] = {tiled ? c.ck->tiled[ti].gs[0][0] : c.ck->gs[0][0],
                               tiled ? c.ck->tiled[ti].gs[1][0] : c.ck->gs[1][0]};
       const int rnt = tiled ? c.rk->nt_t[ti] : c.rk->nt, rsm = tiled ? c.rk->smem_t[ti] : c.rk->smem;

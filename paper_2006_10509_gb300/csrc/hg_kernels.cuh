@@ -1123,7 +1123,9 @@ __global__ void __launch_bounds__(RowCfg<W, TW>::NT, RowCfg<W, TW>::MINB) k_row_
 // (Row-major instances have no minimum of CTAs per SM (0): ptxas then takes 128 registers at 2048,
 // measured faster than any cap, and an explicit minimum of 1 made it take 191 and the pass 30 %
 // longer.  Tiled instances are held to 2 CTAs of 256 threads per SM, which they would exceed.)
-template <int W, bool OUT, int TW = 0>
+// SQ (square items on the tiled field): the strip height W at compile time, as in k_row_gs (the
+// tiled instance's spills, 36-48 bytes per thread at 2048, vanish with it).
+template <int W, bool OUT, int TW = 0, bool SQ = false>
 __global__ void __launch_bounds__(RowCfg<W, TW>::NT, TW ? hg_max(1, 512 / RowCfg<W, TW>::NT) : 0)
     k_row_mp(const __grid_constant__ PassArgs a) {
   using K = RowCfg<W, TW>;
@@ -1147,7 +1149,7 @@ __global__ void __launch_bounds__(RowCfg<W, TW>::NT, TW ? hg_max(1, 512 / RowCfg
         v[s] = row < H ? f[(size_t)row * W + n] : make_float2(0.f, 0.f);
       });
     } else {
-      load_row_slots<K, K::RE, TW>(v, f, t, row0, H);
+      load_row_slots<K, K::RE, TW>(v, f, t, row0, SQ ? W : H);
     }
     FftRun<G, true, 1, typename K::Inv>::run(v, sm, t, a.tw_row);
     for_each_slot<G, K::RM>(t, [&](int s, int b, int n) {
@@ -1185,7 +1187,7 @@ __global__ void __launch_bounds__(RowCfg<W, TW>::NT, TW ? hg_max(1, 512 / RowCfg
         if (row < H) f[(size_t)row * W + n] = v[s];
       });
     } else {
-      store_row_slots<K, K::RE, TW>(v, f, t, row0, H);
+      store_row_slots<K, K::RE, TW>(v, f, t, row0, SQ ? W : H);
     }
   }
 }

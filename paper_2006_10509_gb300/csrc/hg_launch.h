@@ -63,6 +63,7 @@ struct RowKernels {
   // where the row length does not tile so, and for width 16): k_row_mp_init<PROJECT = true>, k_row_mp
   const void* mp_init_t[4];
   const void* mp_t[4][2];
+  const void* mp_sq[2];     // k_row_mp<OUT> on 2-column strips for square items (nullptr: none)
   // generic lengths only (mp_init / mp / gd_bwd are nullptr there): multi-plane GS and gradient
   // descent run one launch per plane through a plan-owned accumulator [slot][H][W] complex64;
   // kernels (PassArgs, int plane, float* accumulator)

@@ -65,6 +65,8 @@ void fill_square(RowKernels& r) {
   if constexpr (row_tileable<N, 2>()) {
     r.gs_sq[0][0] = (const void*)&k_row_gs<N, false, 2, false, 0, true>;
     r.gs_sq[0][1] = (const void*)&k_row_gs<N, true, 2, false, 0, true>;
+    r.mp_sq[0] = (const void*)&k_row_mp<N, false, 2, true>;
+    r.mp_sq[1] = (const void*)&k_row_mp<N, true, 2, true>;
   }
   if constexpr (has_alt_plan<N>() && row_tileable<N, 2, 1>()) {
     r.gs_sq[1][0] = (const void*)&k_row_gs<N, false, 2, false, 1, true>;
@@ -77,6 +79,8 @@ void set_square_attrs() {
   if constexpr (row_tileable<N, 2>()) {
     allow_smem(&k_row_gs<N, false, 2, false, 0, true>, RowCfg<N, 2>::SMEM);
     allow_smem(&k_row_gs<N, true, 2, false, 0, true>, RowCfg<N, 2>::SMEM);
+    allow_smem(&k_row_mp<N, false, 2, true>, RowCfg<N, 2>::SMEM);
+    allow_smem(&k_row_mp<N, true, 2, true>, RowCfg<N, 2>::SMEM);
   }
   if constexpr (has_alt_plan<N>() && row_tileable<N, 2, 1>()) {
     allow_smem(&k_row_gs<N, false, 2, false, 1, true>, RowCfg<N, 2, 1>::SMEM);
