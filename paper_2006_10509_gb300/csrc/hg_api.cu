@@ -1814,6 +1814,9 @@ static hg_status gd_run(hg_plan* p, float* const* phase, const float* const* tar
       }
       const dim3 grow(c.row_blocks(), nb), gcol(c.col_blocks(), nb * P);
       const bool gen = c.rk->gen != nullptr;  // generic row length: one launch per plane
+      // square items: the column passes with the row length at compile time
+      const bool sq = c.H == c.W && c.ck->gd_sq[0] != nullptr;
+      const void* kgd[2] = {sq ? c.ck->gd_sq[0] : c.ck->gd[0], sq ? c.ck->gd_sq[1] : c.ck->gd[1]};
       if (fwd) {
         if (gen) {
           if ((s = launch(p, K_ROW_GD_FWD, c.rk->plane.start[0], pointwise_grid(c, nb), 256, 0, a, st, 0,
@@ -1823,11 +1826,11 @@ static hg_status gd_run(hg_plan* p, float* const* phase, const float* const* tar
         } else if ((s = launch(p, K_ROW_GD_FWD, c.rk->mp_init[0], grow, c.rk->nt, c.rk->smem, a, st)) != HG_OK) {
           return s;
         }
-        if ((s = launch(p, K_COL_GD_FWD, c.ck->gd[0], gcol, c.ck->nt, c.ck->smem, a, st)) != HG_OK) return s;
+        if ((s = launch(p, K_COL_GD_FWD, kgd[0], gcol, c.ck->nt, c.ck->smem, a, st)) != HG_OK) return s;
         if ((s = launch(p, K_FINALIZE, (const void*)&hg::k_finalize<1>, dim3(1, nb), 32, 0, a, st)) != HG_OK) return s;
       }
       if (bwd) {
-        if ((s = launch(p, K_COL_GD_BWD, c.ck->gd[1], gcol, c.ck->nt, c.ck->smem, a, st)) != HG_OK) return s;
+        if ((s = launch(p, K_COL_GD_BWD, kgd[1], gcol, c.ck->nt, c.ck->smem, a, st)) != HG_OK) return s;
         if (gen) {
           if ((s = plane_backs(p, c, K_ROW_GD_BWD, a, grow, st)) != HG_OK ||
               (s = launch(p, K_ROW_GD_BWD, c.rk->plane.grad, pointwise_grid(c, nb), 256, 0, a, st, 0,

@@ -107,6 +107,7 @@ struct ColKernels {
   const void* fft[2][2];    // k_col_fft<INV><POST>
   const void* ospr[3];      // k_col_ospr: [0] start only, [1] finish + start, [2] finish only
   const void* gd[2];        // k_col_gd<BWD = false / true>
+  const void* gd_sq[2];     // the same for square items (row length at compile time)
   void (*set_attrs)();
   TwiddleLayout tw;         // twiddle tables of length H
   const GenPlan* gen;       // generic kernels: their run-time plan (nullptr for compiled lengths)

@@ -260,6 +260,8 @@ ColKernels make_col() {
   c.ospr[2] = (const void*)&k_col_ospr<N, true, false>;
   c.gd[0] = (const void*)&k_col_gd<N, false>;
   c.gd[1] = (const void*)&k_col_gd<N, true>;
+  c.gd_sq[0] = (const void*)&k_col_gd<N, false, true>;
+  c.gd_sq[1] = (const void*)&k_col_gd<N, true, true>;
   c.tw = make_tw<N>();
   return c;
 }
@@ -316,6 +318,8 @@ void set_col_attrs(const ColKernels& c) {
   allow_smem(&k_col_ospr<HG_LEN, true, false>, c.smem_ospr);
   allow_smem(&k_col_gd<HG_LEN, false>, c.smem);
   allow_smem(&k_col_gd<HG_LEN, true>, c.smem);
+  allow_smem(&k_col_gd<HG_LEN, false, true>, c.smem);
+  allow_smem(&k_col_gd<HG_LEN, true, true>, c.smem);
 }
 
 }  // namespace
