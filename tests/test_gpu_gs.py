@@ -55,11 +55,15 @@ CASES = [
     # 2-column tiles: Fresnel chirps on square and non-square items
     (512, 512, 0, 0.08),
     (2048, 512, 4, 0.1),
-    # generic kernels (lengths without a compiled instance), alone and mixed with compiled ones
+    # common SLM sizes (compiled 720 / 1200 / 1280 / 2160 / 3840; 1000 on the generic kernels)
     (1024, 1280, 4, None),
     (720, 1280, 0, None),
     (2160, 3840, 4, None),
     (1000, 1200, 0, 0.1),
+    # generic kernels (lengths without a compiled instance), alone and mixed with compiled ones
+    (1000, 1125, 4, None),
+    (1500, 2000, 0, 0.1),
+    (2000, 1024, 8, None),
     (27, 125, 8, None),
     (3, 5, 2, None),
     (1, 8, 0, None),

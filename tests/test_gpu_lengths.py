@@ -37,7 +37,7 @@ def _intensities(h, w, seed, planes=3):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("h, w, levels", [(100, 120, 0), (90, 1280, 4), (1000, 64, 0)])
+@pytest.mark.parametrize("h, w, levels", [(100, 120, 0), (90, 1280, 4), (1000, 64, 0), (60, 1000, 4)])
 def test_multiplane_gs_generic_lengths_one_step_and_curve(h, w, levels):
     import torch
 
@@ -79,7 +79,7 @@ def test_multiplane_gs_generic_lengths_one_step_and_curve(h, w, levels):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("h, w, zs", [(100, 120, ZS), (45, 1280, ZS[:2]), (128, 27, None)])
+@pytest.mark.parametrize("h, w, zs", [(100, 120, ZS), (45, 1280, ZS[:2]), (128, 27, None), (45, 1000, ZS[:2])])
 def test_gd_generic_lengths_gradient_and_adam(h, w, zs):
     import torch
 

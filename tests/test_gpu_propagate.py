@@ -15,10 +15,10 @@ LAM, PITCH = 532e-9, 8e-6
 
 SIZES = [(8, 8), (16, 32), (64, 64), (256, 256), (12, 15), (30, 60), (120, 64), (15, 8), (60, 1920),
          (864, 1536), (1080, 1920), (2048, 2048), (4096, 256), (512, 4096),
-         # lengths without a compiled instance (the generic kernels), alone and mixed with compiled ones:
-         # common SLM sizes, odd and degenerate sizes, the longest generic lengths
-         (1024, 1280), (720, 1280), (2160, 3840), (1000, 1200), (1, 1), (1, 8), (3, 5), (27, 125),
-         (243, 100), (2, 4000), (4050, 6), (3125, 18)]
+         # common SLM sizes (compiled since), then lengths without a compiled instance (the generic
+         # kernels), alone and mixed with compiled ones: odd and degenerate sizes, the longest ones
+         (1024, 1280), (720, 1280), (2160, 3840), (1000, 1200), (1500, 2000), (1000, 1125), (1, 1), (1, 8),
+         (3, 5), (27, 125), (243, 100), (2, 4000), (4050, 6), (3125, 18)]
 
 
 def _field(h, w, seed):
