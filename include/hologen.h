@@ -41,8 +41,8 @@
  *    device, or a buffer that does not fit in its allocation, is rejected with HG_ERR_INVALID_ARG.
  *  - A plan is used from one host thread at a time.  Different plans are independent.
  *  - Supported FFT lengths (H and W): every n = 2^a 3^b 5^c with 1 <= n <= 4096 (137 lengths).
- *    8, 16, 32, 64, 128, 256, 512, 1024, 2048, 4096, 12, 15, 30, 60, 120, 720, 864, 1080, 1200,
- *    1280, 1536, 1920, 2160 and 3840 have compiled kernels (radix plans fixed at build time, the field in registers between
+ *    8, 16, 32, 64, 128, 256, 512, 1024, 2048, 4096, 12, 15, 30, 60, 120, 720, 864, 1080, 1152,
+ *    1200, 1280, 1440, 1536, 1600, 1920, 2160, 2560 and 3840 have compiled kernels (radix plans fixed at build time, the field in registers between
  *    stages); the others run on generic kernels (a run-time radix plan, the tile in shared memory
  *    between stages; slower, same arithmetic).  Other sizes give HG_ERR_UNSUPPORTED_SIZE.
  */

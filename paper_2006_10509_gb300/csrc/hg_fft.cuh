@@ -379,13 +379,17 @@ HG_PLAN(864, 16, 6, 9)
 HG_PLAN(1080, 8, 9, 15)
 HG_PLAN(1536, 16, 16, 6)
 HG_PLAN(1920, 16, 8, 15)
-// common SLM sides (1280 x 720, 1280 x 1024, 1920 x 1200, 3840 x 2160): measured on GB300 two to
-// four times faster per pixel than the generic kernels; stage orders from a bank-conflict model
-// of every tile shape
+// common SLM sides (1280 x 720, 1280 x 1024, 1920 x 1152, 1920 x 1200, 2560 x 1440, 2560 x 1600,
+// 3840 x 2160): measured on GB300 two to four times faster per pixel than the generic kernels;
+// stage orders from a bank-conflict model of every tile shape
 HG_PLAN(720, 16, 9, 5)
+HG_PLAN(1152, 16, 9, 8)
 HG_PLAN(1200, 16, 5, 15)
 HG_PLAN(1280, 16, 5, 16)
+HG_PLAN(1440, 16, 6, 15)
+HG_PLAN(1600, 16, 10, 10)
 HG_PLAN(2160, 16, 9, 15)
+HG_PLAN(2560, 16, 10, 16)
 HG_PLAN(3840, 16, 15, 16)
 #undef HG_PLAN
 

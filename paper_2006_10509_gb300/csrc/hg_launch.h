@@ -117,7 +117,7 @@ struct ColKernels {
 #define HG_FOR_EACH_LENGTH(X) \
   X(8) X(16) X(32) X(64) X(128) X(256) X(512) X(1024) X(2048) X(4096) \
   X(12) X(15) X(30) X(60) X(120) X(864) X(1080) X(1536) X(1920) \
-  X(720) X(1200) X(1280) X(2160) X(3840)
+  X(720) X(1152) X(1200) X(1280) X(1440) X(1600) X(2160) X(2560) X(3840)
 
 #define HG_DECLARE_LEN(N)                  \
   const RowKernels& row_kernels_##N();     \

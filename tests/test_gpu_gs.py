@@ -55,7 +55,11 @@ CASES = [
     # 2-column tiles: Fresnel chirps on square and non-square items
     (512, 512, 0, 0.08),
     (2048, 512, 4, 0.1),
-    # common SLM sizes (compiled 720 / 1200 / 1280 / 2160 / 3840; 1000 on the generic kernels)
+    # common SLM sizes (compiled 720 / 1152 / 1200 / 1280 / 1440 / 1600 / 2160 / 2560 / 3840; 1000
+    # on the generic kernels)
+    (1152, 1920, 4, None),
+    (1440, 2560, 0, None),
+    (1600, 2560, 8, None),
     (1024, 1280, 4, None),
     (720, 1280, 0, None),
     (2160, 3840, 4, None),
